@@ -1,0 +1,250 @@
+/*
+ * spmv.h -- C ABI of a GB300 (sm_103a) library for the CRS sparse matrix-vector
+ * multiply of Schubert, Fehske, Hager and Wellein, "Hybrid-parallel sparse
+ * matrix-vector multiplication with explicit communication overlap on current
+ * multicore-based systems" (2011).
+ *
+ * Storage (Sect. 1.2): a matrix with n_rows rows is given by three arrays,
+ *   row_ptr[n_rows+1]  starting offset of every row, row_ptr[0] == 0,
+ *                      nondecreasing, row_ptr[n_rows] == nnz;
+ *   col_idx[nnz]       column of every stored entry, 0 <= col_idx[k] < n_cols;
+ *   val[nnz]           value of every stored entry, row by row.
+ * Indices are 0-based (the paper's Fortran listing is 1-based).  Columns within a
+ * row need not be sorted and repeated (row, col) entries are summed.
+ *
+ * Conventions for every call:
+ *   - int32 indices; n_rows, n_cols, nnz < 2^31.
+ *   - Vectors (x, y, g, grad_x, grad_val, X, Y) are caller-owned DEVICE pointers,
+ *     borrowed for the duration of the call only.  Every compute call is
+ *     asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  A call returns once its work is enqueued.
+ *   - Handles own device copies of what they hold and are not safe for concurrent
+ *     applies from several host threads.
+ *   - Errors are returned status codes; nothing is thrown across the ABI.  Errors
+ *     of already-enqueued kernels surface as SPMV_ERR_CUDA on a later call.
+ *   - beta == 0 means y is not read (NaN or Inf in y does not propagate).
+ *   - Summation order within a row is unspecified; results match the FP64 row sum
+ *     of Listing 1 to within |y - y_ref|_i <= 1e-13 * sum_j |a_ij x_j| for FP64
+ *     operands and <= 1e-6 * sum_j |a_ij x_j| for FP32-stored operands, and are
+ *     bit-exact when A and x are integer-valued with every partial sum exact.
+ */
+#ifndef SPMV_H
+#define SPMV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,    /* null pointer, bad size, shape or dtype       */
+    SPMV_ERR_INVALID_INDEX = 2,  /* row_ptr not a valid CRS offset array, or a
+                                    column index outside [0, n_cols)             */
+    SPMV_ERR_CUDA = 3,           /* a CUDA runtime call or kernel failed          */
+    SPMV_ERR_ALLOC = 4,          /* device or host allocation failed              */
+    SPMV_ERR_UNSUPPORTED = 5,    /* combination not provided by this library      */
+    SPMV_ERR_TIMEOUT = 6,        /* a bounded on-device wait gave up              */
+    SPMV_ERR_NOT_CONVERGED = 7   /* iterative solver hit its iteration cap        */
+} spmv_status;
+
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1 } spmv_dtype;
+
+typedef struct spmv_matrix *spmv_handle;
+typedef struct spmv_split *spmv_split_handle;
+typedef struct spmv_batch *spmv_batch_handle;
+
+/* Human-readable name of a status code (static storage). */
+const char *spmv_status_string(spmv_status s);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t spmv_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Matrix handle (Sect. 1.2 storage; Listing 1 kernel)                        */
+/* ------------------------------------------------------------------------ */
+
+/* Create a handle from CRS arrays.  The arrays are validated (row_ptr[0] == 0,
+ * nondecreasing, row_ptr[n_rows] == nnz, 0 <= col_idx < n_cols) and copied into
+ * handle-owned device memory; the caller keeps ownership of its arrays.
+ * is_device_ptr != 0: the three arrays are device pointers, else host pointers.
+ * val_t selects FP64 or FP32 storage of the values.  The handle also derives,
+ * from the row-length histogram, the kernel plan used by every apply (the tile
+ * table and the per-thread nonzero count).  stream orders the copies; the call
+ * synchronises the stream before returning.
+ * Errors: SPMV_ERR_INVALID_ARG (null out, negative sizes, null arrays with
+ * nnz > 0), SPMV_ERR_INVALID_INDEX (bad row_ptr or column), SPMV_ERR_ALLOC,
+ * SPMV_ERR_CUDA.  *out is NULL on error. */
+spmv_status spmv_create(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                        const int32_t *row_ptr, const int32_t *col_idx, const void *val,
+                        spmv_dtype val_t, int is_device_ptr, void *stream);
+
+/* Release a handle and everything it owns (NULL is ignored).  Synchronises the
+ * device work that may still use it. */
+void spmv_destroy(spmv_handle h);
+
+/* Replace the stored values (same sparsity pattern) from a device pointer of
+ * type t; t may differ from the handle's storage type only as FP64 -> FP32
+ * storage or FP32 -> FP64 storage (converted on the device).  Asynchronous. */
+spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *stream);
+
+/* Shape and plan of a handle.  plan[0..7] receives: kernel family (0 = nnz-split
+ * tile kernel, 1 = row-vector kernel), nonzeros per thread E, threads per CTA,
+ * number of tiles, rows per tile cap, threads per row for the row-vector kernel,
+ * number of rows longer than a tile, value dtype.  Any output may be NULL. */
+spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64_t *nnz,
+                          int32_t *plan);
+
+/* Row-length histogram used by the autotuner: counts[L] = rows with exactly L
+ * entries for L < nbins - 1, counts[nbins-1] = rows with >= nbins-1 entries.
+ * counts is a HOST array of nbins int64. */
+spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
+
+/* Override the autotuner's choice of kernel family and per-thread work.
+ * family: 0 = nnz-split tile kernel, 1 = row-vector kernel; param = E (odd,
+ * 3..31) for family 0, threads per row (1,2,4,8,16,32) for family 1; 0 keeps the
+ * tuned value.  Results are unchanged up to summation order. */
+spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
+
+/* Plain spMVM, Listing 1 generalised: y = alpha*A*x + beta*y.
+ * x: n_cols entries of type xt; y: n_rows entries of type yt.  Supported
+ * (value, x, y) types: (F64, F64, F64), (F32, F32, F32), (F32, F32, F64).  FP32
+ * operands are multiplied and accumulated in at least FP64-class precision.
+ * x and y must not overlap. */
+spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt,
+                       double beta, void *y, spmv_dtype yt, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Local/nonlocal split form (Sect. 3.2 distribution; Sect. 3.4-3.5, Eq. 2)  */
+/* ------------------------------------------------------------------------ */
+
+/* Build the split plan of a square matrix once (the bookkeeping of Sect. 3.2):
+ * nblocks contiguous row blocks (block_row_start: nblocks+1 HOST entries with
+ * start[0] = 0, start[nblocks] = n_rows, nondecreasing; NULL = nonzeros balanced,
+ * block b starting at the first row whose offset is >= ceil(b*nnz/nblocks)).  The
+ * right-hand side is distributed like the rows, so column j is local to block b
+ * iff start[b] <= j < start[b+1].  For each block the plan holds its halo map
+ * (sorted distinct nonlocal columns), the local part A_loc and the nonlocal part
+ * A_nl with columns renumbered into the concatenated halo buffer.
+ * halo_count_out (optional HOST array of nblocks) receives the halo sizes.
+ * The split handle references h, which must outlive it. */
+spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nblocks,
+                              const int32_t *block_row_start, int32_t *halo_count_out);
+void spmv_split_destroy(spmv_split_handle hs);
+
+/* Copy the plan out to HOST arrays (each optional): block_start[nblocks+1],
+ * halo_count[nblocks], halo_map[total halo], nnz_local[nblocks],
+ * nnz_nonlocal[nblocks]; *total_halo receives the halo length. */
+spmv_status spmv_split_get_plan(spmv_split_handle hs, int32_t *nblocks, int32_t *block_start,
+                                int32_t *halo_count, int64_t *total_halo, int32_t *halo_map,
+                                int64_t *nnz_local, int64_t *nnz_nonlocal);
+
+/* Split spMVM (task-mode analogue of Sect. 3.5, Fig. kernel_schemes (c)):
+ *   s_compute: record "x ready";
+ *   s_comm:    wait for it, gather halo[h] = x[halo_map[h]] (the stand-in for the
+ *              MPI exchange), record "halo ready";
+ *   s_compute: y = beta*y + alpha*A_loc*x over all blocks (overlaps the gather),
+ *              wait for "halo ready", then y += alpha*A_nl*halo.
+ * The result vector is written twice, as in Eq. 2.  FP64 x and y only.
+ * s_comm may equal s_compute (naive overlap of Sect. 3.4 on one stream). */
+spmv_status spmv_apply_split(spmv_split_handle hs, double alpha, const double *x, double beta,
+                             double *y, void *s_compute, void *s_comm);
+
+/* Copy the halo buffer filled by the last spmv_apply_split to a HOST array of
+ * total-halo doubles (synchronises s). */
+spmv_status spmv_split_get_halo(spmv_split_handle hs, double *halo_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Block vectors                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Y = alpha*A*X + beta*Y for nrhs right-hand sides stored interleaved:
+ * X[j*nrhs + r], Y[i*nrhs + r] (row-major, leading dimension nrhs).
+ * 1 <= nrhs <= 64.  vt: SPMV_F64 (X, Y FP64; FP64 values) only. */
+spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X, double beta,
+                       void *Y, spmv_dtype vt, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Reverse pass                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Gradients of f = g^T y with y = alpha*A(val)*x:
+ *   grad_x[j]   = alpha * sum_i a_ij g_i   (alpha*A^T g; n_cols entries), through a
+ *                 transposed CRS built once on the device and kept in the handle;
+ *   grad_val[k] = alpha * g[row(k)] * x[col_idx[k]]   (nnz entries, CRS order).
+ * Both outputs are overwritten; either may be NULL.  FP64 handles take FP64 g,
+ * x and outputs; FP32-storage handles take FP32 g, x and write FP32 outputs. */
+spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void *x,
+                          void *grad_x, void *grad_val, void *stream);
+
+/* Copy the transposed structure to HOST arrays (builds it if needed):
+ * rowT_ptr[n_cols+1], colT_idx[nnz] (row of A of each entry), perm[nnz] (position
+ * in A of each entry of A^T).  Within a row of A^T, entries are in increasing
+ * position of A. */
+spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_idx,
+                               int32_t *perm, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched persistent launch                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Group count matrix handles (all FP64 or all FP32 storage) into one batch whose
+ * apply is a single persistent kernel launch over the tiles of every matrix,
+ * captured once into a CUDA graph and replayed.  The per-thread work E and the
+ * tile size come from the combined row-length histogram.  The handles must
+ * outlive the batch. */
+spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spmv_handle *mats);
+void spmv_batched_destroy(spmv_batch_handle b);
+
+/* y_m = alpha*A_m*x_m + beta*y_m for every matrix m.  x and y are HOST arrays of
+ * count device pointers (vector types follow the storage type: FP64 or FP32).
+ * When the pointer set or alpha/beta differ from the previous call the device
+ * pointer table is rewritten and the graph re-instantiated; otherwise the
+ * instantiated graph is replayed on stream. */
+spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *const *x,
+                               double beta, void *const *y, void *stream);
+
+/* plan[0..3]: E, threads per CTA, total tiles, persistent grid size. */
+spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan);
+
+/* ------------------------------------------------------------------------ */
+/* Mixed-precision iterative refinement CG                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Solve A x = b for SPD A (FP64 handle) by iterative refinement:
+ *   outer (FP64): r = b - A x (FP64 spMVM), ||r||_2, stop when
+ *                 ||r||_2 <= outer_tol*||b||_2 or after max_outer steps;
+ *   inner (FP32 storage): CG on A d = r with FP32 values and vectors, FP64
+ *                 accumulation inside the spMVM and the dot products, stopped at
+ *                 relative residual inner_tol or max_inner iterations;
+ *   update (FP64): x += d.
+ * b, x: device FP64 vectors of n_rows; x is overwritten (x0 = 0).
+ * stats (optional HOST array of 4 doubles): outer steps, total inner iterations,
+ * final relative residual ||b - A x||/||b|| (FP64, on the device), seconds.
+ * Returns SPMV_ERR_NOT_CONVERGED if the outer cap is reached first.
+ * Synchronises the stream (one scalar read per inner iteration). */
+spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_tol,
+                       int32_t max_outer, double inner_tol, int32_t max_inner,
+                       double *stats, void *stream);
+
+/* FP64 conjugate gradients on the device with the FP64 spMVM (the comparison
+ * solver for spmv_ir_cg): x0 = 0, stop at ||r||_2 <= tol*||b||_2 (recursive
+ * residual) or max_iter.  stats as for spmv_ir_cg (outer steps = 1). */
+spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                    double *stats, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Error word                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Read and clear the handle's device error word (synchronises stream).  Returns
+ * SPMV_ERR_TIMEOUT if a bounded on-device wait gave up since the last check,
+ * SPMV_OK otherwise. */
+spmv_status spmv_check_device_error(spmv_handle h, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_H */

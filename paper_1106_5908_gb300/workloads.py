@@ -1,0 +1,271 @@
+"""Seeded synthetic CRS matrices and vectors shaped like the paper's workloads.
+
+This module only draws inputs.  It contains none of the spMVM arithmetic, imports
+neither the oracle nor the CUDA binding, and is the one module both sides share.
+All generators use numpy's PCG64 (``np.random.default_rng(seed)``) and return
+0-based CRS arrays ``(row_ptr int32, col_idx int32, val float64)`` with columns
+sorted within each row unless stated otherwise.
+
+Stand-ins for the paper's matrices (Sect. 1.3.1), which are not available here:
+  * ``hamiltonian_like`` for the HMeP Holstein-Hubbard matrix (symmetric, banded
+    plus scattered entries, N_nzr around 13-15);
+  * ``laplace3d`` for the sAMG Poisson matrix (N_nzr about 7);
+  * ``stencil27`` for the higher-N_nzr regime (UHBR has N_nzr about 123, not
+    reproduced).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# Fixed seeds of the synthetic workloads.
+SEED_C1_X = 1101
+SEED_C1_XINT = 1102
+SEED_C2_MATRIX = 2201
+SEED_C2_X = 2202
+SEED_C3_B = 3301
+SEED_C4_X = 4401
+SEED_C4_BATCH = 4402
+SEED_C5_VAL = 5501
+SEED_C5_X = 5502
+SEED_C5_G = 5503
+
+
+@dataclass
+class CRS:
+    row_ptr: np.ndarray  # int32, n_rows + 1
+    col_idx: np.ndarray  # int32, nnz
+    val: np.ndarray      # float64, nnz
+    n_cols: int
+
+    @property
+    def n_rows(self) -> int:
+        return int(self.row_ptr.size - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def astuple(self):
+        return self.row_ptr, self.col_idx, self.val
+
+
+def _row_ptr_from_counts(counts: np.ndarray) -> np.ndarray:
+    rp = np.zeros(counts.size + 1, np.int64)
+    np.cumsum(counts, out=rp[1:])
+    return rp.astype(np.int32)
+
+
+def _stencil(shape, offsets, diag_value, off_value, vals=None) -> CRS:
+    """Truncated (Dirichlet) stencil on a lexicographic grid, first axis fastest.
+    ``offsets`` are tuples in the order of ``shape`` listed so that the linear
+    column offset increases; entries outside the grid are dropped."""
+    dims = len(shape)
+    n = int(np.prod(shape))
+    idx = np.arange(n, dtype=np.int64)
+    coords = []
+    rem = idx
+    for d in range(dims):
+        coords.append(rem % shape[d])
+        rem = rem // shape[d]
+    strides = [int(np.prod(shape[:d])) for d in range(dims)]
+    cols = np.full((n, len(offsets)), -1, dtype=np.int64)
+    for m, off in enumerate(offsets):
+        ok = np.ones(n, bool)
+        lin = idx.copy()
+        for d in range(dims):
+            c = coords[d] + off[d]
+            ok &= (c >= 0) & (c < shape[d])
+            lin += off[d] * strides[d]
+        cols[ok, m] = lin[ok]
+    mask = cols >= 0
+    counts = mask.sum(axis=1)
+    col_idx = cols[mask].astype(np.int32)  # row-major flatten keeps rows, columns ascend
+    if vals is None:
+        is_diag = np.zeros((n, len(offsets)), bool)
+        for m, off in enumerate(offsets):
+            if all(o == 0 for o in off):
+                is_diag[:, m] = True
+        val = np.where(is_diag[mask], diag_value, off_value).astype(np.float64)
+    else:
+        val = vals(int(mask.sum()))
+    return CRS(_row_ptr_from_counts(counts), col_idx, val, n)
+
+
+def _sorted_offsets(dims, radius_set):
+    offs = [o for o in radius_set]
+    # order by linear offset: last axis most significant
+    def key(o):
+        return tuple(reversed(o))
+    return sorted(offs, key=key)
+
+
+def laplace2d(nx: int, ny: int | None = None) -> CRS:
+    """2D 5-point Laplacian, diagonal 4, off-diagonals -1, Dirichlet boundary
+    (truncated stencil), x fastest."""
+    ny = nx if ny is None else ny
+    offs = [(0, -1), (-1, 0), (0, 0), (1, 0), (0, 1)]
+    return _stencil((nx, ny), _sorted_offsets(2, offs), 4.0, -1.0)
+
+
+def laplace3d(n: int) -> CRS:
+    """3D 7-point Laplacian on an n^3 grid, diagonal 6, off-diagonals -1."""
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    return _stencil((n, n, n), _sorted_offsets(3, offs), 6.0, -1.0)
+
+
+def stencil27(n: int, seed: int = SEED_C5_VAL) -> CRS:
+    """27-point pattern on an n^3 grid (diagonal included), values N(0,1), not
+    symmetric."""
+    offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    rng = np.random.default_rng(seed)
+    return _stencil((n, n, n), _sorted_offsets(3, offs), 0.0, 0.0,
+                    vals=lambda m: rng.standard_normal(m))
+
+
+def _distinct_draw(rng, avail, counts, kmax):
+    """For every row r draw counts[r] distinct offsets from [0, avail[r]) with
+    Floyd's subset algorithm, vectorised over rows.  Returns an int64 array of
+    shape (rows, kmax) holding the offsets sorted ascending, padded with -1."""
+    n = avail.size
+    counts = np.minimum(counts, avail)
+    out = np.full((n, kmax), -1, np.int64)
+    for m in range(kmax):
+        act = np.nonzero(counts > m)[0]
+        if act.size == 0:
+            break
+        # Floyd: for j = avail-k+m, draw t in [0, j]; take j if t was drawn already
+        j = avail[act] - counts[act] + m
+        t = rng.integers(0, j + 1, dtype=np.int64)
+        seen = (out[act, :m] == t[:, None]).any(axis=1) if m else np.zeros(act.size, bool)
+        out[act, m] = np.where(seen, j, t)
+    big = np.iinfo(np.int64).max
+    srt = np.sort(np.where(out < 0, big, out), axis=1)
+    return np.where(srt == big, -1, srt)
+
+
+def hamiltonian_like(n: int, seed: int = SEED_C2_MATRIX, band: int = 64,
+                     mean_len: float = 6.0, min_len: int = 2, max_len: int = 16) -> CRS:
+    """Symmetric Hamiltonian-like matrix (stand-in for HMeP).
+
+    Upper-triangle row length l_i = clip(Poisson(mean_len), min_len, max_len);
+    ceil(l_i/2) distinct columns from (i, min(i+band, n-1)] and floor(l_i/2)
+    distinct columns from [i+band+1, n); a shortfall in one range moves to the
+    other; values N(0,1).  The upper part is mirrored to the lower triangle and a
+    N(0,1) diagonal is added; columns are sorted within rows."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n, dtype=np.int64)
+    L = np.clip(rng.poisson(mean_len, n), min_len, max_len).astype(np.int64)
+    near_avail = np.minimum(band, n - 1 - i)
+    far_avail = np.maximum(0, n - (i + band + 1))
+    n_near = (L + 1) // 2
+    n_far = L // 2
+    over = np.maximum(0, n_near - near_avail)
+    n_near -= over
+    n_far += over
+    over = np.maximum(0, n_far - far_avail)
+    n_far -= over
+    n_near = np.minimum(near_avail, n_near + over)
+    near = _distinct_draw(rng, near_avail, n_near, max_len)
+    far = _distinct_draw(rng, far_avail, n_far, max_len)
+    # upper part of every row, columns ascending (near < far), row-major order
+    up = np.concatenate([np.where(near >= 0, near + i[:, None] + 1, -1),
+                         np.where(far >= 0, far + i[:, None] + band + 1, -1)], axis=1)
+    keep = up >= 0
+    n_up = keep.sum(axis=1)
+    up_c = up[keep]
+    up_r = np.repeat(i, n_up)
+    up_v = rng.standard_normal(up_c.size)
+    diag_v = rng.standard_normal(n)
+    # mirror to the lower triangle, add the diagonal; scipy's COO -> CSR conversion
+    # is a counting sort by row, after which columns are sorted within rows
+    import scipy.sparse as sp
+    rows = np.concatenate([up_r, up_c, i]).astype(np.int32)
+    cols = np.concatenate([up_c, up_r, i]).astype(np.int32)
+    vals = np.concatenate([up_v, up_v, diag_v])
+    m = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    m.sort_indices()
+    return CRS(m.indptr.astype(np.int32), m.indices.astype(np.int32),
+               m.data.astype(np.float64), n)
+
+
+def random_csr(n_rows: int, n_cols: int, seed: int, max_len: int = 8, empty_frac: float = 0.2,
+               dup_frac: float = 0.1, sort_cols: bool = False, integer: bool = False,
+               long_rows: int = 0, long_len: int = 0) -> CRS:
+    """Small irregular CRS for tests: some empty rows, repeated (row, col) entries,
+    unsorted columns; optionally integer values in [-4, 4] and a few long rows."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, max_len + 1, n_rows)
+    lens[rng.random(n_rows) < empty_frac] = 0
+    if long_rows and n_rows:
+        pick = rng.choice(n_rows, size=min(long_rows, n_rows), replace=False)
+        lens[pick] = long_len
+    if n_cols == 0:
+        lens[:] = 0
+    nnz = int(lens.sum())
+    cols = rng.integers(0, max(n_cols, 1), nnz) if nnz else np.zeros(0, np.int64)
+    # plant repeats: copy a column from earlier in the same row
+    rp = _row_ptr_from_counts(lens).astype(np.int64)
+    if nnz:
+        row_of = np.repeat(np.arange(n_rows), lens)
+        pos = np.arange(nnz) - rp[row_of]
+        cand = (pos > 0) & (rng.random(nnz) < dup_frac)
+        cols[cand] = cols[np.nonzero(cand)[0] - 1]
+        if sort_cols:
+            order = np.lexsort((cols, row_of))
+            cols = cols[order]
+    if integer:
+        val = rng.integers(-4, 5, nnz).astype(np.float64)
+    else:
+        val = rng.standard_normal(nnz)
+    return CRS(rp.astype(np.int32), cols.astype(np.int32), val, n_cols)
+
+
+def uniform(n: int, seed: int, lo: float = -1.0, hi: float = 1.0, shape=None) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, n if shape is None else shape)
+
+
+def integers(n: int, seed: int, lo: int = -8, hi: int = 8) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, n).astype(np.float64)
+
+
+def truncated_laplace2d(n: int) -> CRS:
+    """5-point Laplacian on the floor(sqrt n) x ceil(n/floor(sqrt n)) grid, cut to
+    its leading n x n block (rows and columns >= n dropped)."""
+    nx = max(1, int(math.isqrt(n)))
+    ny = -(-n // nx)
+    full = laplace2d(nx, ny)
+    rp = full.row_ptr[: n + 1].astype(np.int64)
+    cols = full.col_idx[: rp[-1]]
+    vals = full.val[: rp[-1]]
+    keep = cols < n
+    row_of = np.repeat(np.arange(n), np.diff(rp))
+    counts = np.bincount(row_of[keep], minlength=n)
+    return CRS(_row_ptr_from_counts(counts), cols[keep].astype(np.int32), vals[keep], n)
+
+
+def batch_sizes(count: int = 256, seed: int = SEED_C4_BATCH, lo: int = 1000, hi: int = 200000):
+    rng = np.random.default_rng(seed)
+    return rng.integers(lo, hi + 1, count)
+
+
+def batch_matrix(m: int, n: int, seed: int = SEED_C4_BATCH) -> CRS:
+    """Matrix m of the uneven batch: even m a truncated 2D 5-point Laplacian, odd m
+    a Hamiltonian-like pattern, both of order n."""
+    if m % 2 == 0:
+        return truncated_laplace2d(int(n))
+    return hamiltonian_like(int(n), seed=seed * 1000 + m)
+
+
+# Shapes of the five synthetic configurations.
+C1_GRID = 256          # 2D 5-point, N = 65,536
+C2_N = 4_194_304       # Hamiltonian-like, N = 4,194,304
+C3_GRID = 160          # 3D 7-point, N = 4,096,000
+C4_NRHS = (1, 4, 8, 16, 32)
+C4_COUNT = 256
+C5_GRID = 128          # 3D 27-point, N = 2,097,152
+C5_FD_GRID = 16
