@@ -1,0 +1,435 @@
+"""Benchmark of the CRS spMVM hot path on GB300.
+
+One step is one pass of the hot path over the Hamiltonian-like matrix
+(N = 4,194,304, about 13 entries per row, FP64): the plain product y = A x, the
+local/nonlocal split product over 8 nonzero-balanced row blocks with the halo
+gather on a second stream, and the FP32-storage product.  The metric is
+algorithmic GB/s (bytes every operand must move once, see model.py) with GFLOP/s
+beside it, against the measured HBM copy bandwidth.  Inputs are resident in HBM
+when the timed region starts; the matrix (657 MB) is larger than L2, which is not
+flushed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica (the path is not sharded);
+the value is the bytes of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1106_5908_gb300 import model  # noqa: E402
+from paper_1106_5908_gb300 import workloads as W  # noqa: E402
+
+METRIC = "spMVM GB/s & GFLOP/s vs 8 TB/s HBM roofline; FP32-IR/block/adjoint vs plain FP64"
+UNIT = "GB/s"
+
+# DRAM traffic of one launch of the plain FP64 tile kernel on this workload, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
+# the kernel source whose hash is recorded with it.
+TRAFFIC = {"kernel_hash": None, "bytes_per_launch": None}
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tile_kernel.cuh", "common.cuh", "internal.h", "k_tile_f64.cu"):
+        with open(os.path.join(ROOT, "paper_1106_5908_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+
+def c2_workload():
+    A = W.hamiltonian_like(W.C2_N, seed=W.SEED_C2_MATRIX)
+    x = W.uniform(A.n_rows, W.SEED_C2_X)
+    return A, x
+
+
+def step_bytes(A, total_halo):
+    n, nnz = A.n_rows, A.nnz
+    b_plain = model.bytes_plain(n, n, nnz)
+    b_split = model.bytes_split(n, n, nnz, total_halo)
+    b_f32 = model.bytes_plain(n, n, nnz, val_bytes=4, x_bytes=4, y_bytes=4)
+    return b_plain, b_split, b_f32
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank):
+    import oracle
+    if rank != 0:
+        return
+    A, x = c2_workload()
+    n, nnz = A.n_rows, A.nnz
+    bs = oracle.split_blocks(A.row_ptr, 8)
+    cnt, _, _, _ = oracle.split_halo(A.row_ptr, A.col_idx, A.n_cols, bs)
+    b_plain, b_split, b_f32 = step_bytes(A, int(cnt.sum()))
+    rp, ci, v = A.row_ptr, A.col_idx, A.val
+    v32 = v.astype(np.float32).astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    y = np.empty(n)
+
+    def step():
+        oracle.spmv_omp(rp, ci, v, x, y)        # plain
+        oracle.spmv_omp(rp, ci, v, x, y)        # split form: same row sums
+        oracle.spmv_omp(rp, ci, v32, x32, y)    # FP32-stored operands, FP64 sums
+    threads = oracle.num_threads()
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = (b_plain + b_split + b_f32) * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"Hamiltonian-like N={n} nnz={nnz}: plain + split(8) + FP32-storage",
+                   "parallelism": "host cores (OpenMP over rows)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"full matrix, {args.steps} steps of three FP64 row-sum passes"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def cpu_baseline(A, x, b_plain, budget_s=10.0):
+    """The oracle as it stands (OpenMP over rows, Sect. 2) timed on the host cores
+    on the plain FP64 product of the full matrix, repeated for about budget_s."""
+    import oracle
+    y = np.empty(A.n_rows)
+    threads = oracle.spmv_omp(A.row_ptr, A.col_idx, A.val, x, y)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.spmv_omp(A.row_ptr, A.col_idx, A.val, x, y)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or reps >= 2000:
+            break
+    return {"value": b_plain * reps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"plain FP64 product of the full matrix, {reps} repetitions in {dt:.1f} s"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1106_5908_gb300 import Matrix
+    from paper_1106_5908_gb300.build import build as build_lib
+
+    torch.cuda.set_device(local_rank)
+    build_lib()
+    dev = torch.device("cuda", local_rank)
+    A, x = c2_workload()
+    n, nnz = A.n_rows, A.nnz
+    M64 = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+    M32 = Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols)
+    SP = M64.split(8)
+    total_halo = int(SP.plan()["total_halo"])
+    b_plain, b_split, b_f32 = step_bytes(A, total_halo)
+    b_step = b_plain + b_split + b_f32
+    flops_step = 3 * model.flops(nnz)
+
+    s1 = torch.cuda.Stream(device=dev)
+    s2 = torch.cuda.Stream(device=dev)
+    xd = torch.as_tensor(x).to(dev)
+    x32 = xd.float()
+    y64 = torch.empty(n, dtype=torch.float64, device=dev)
+    ys = torch.empty(n, dtype=torch.float64, device=dev)
+    y32 = torch.empty(n, dtype=torch.float32, device=dev)
+    K, Wm = args.steps, args.warmup
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+          for k in ("plain", "split", "f32")}
+    ev_end = {k: [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+              for k in ("plain", "split", "f32")}
+
+    def step(i=None):
+        with torch.cuda.stream(s1):
+            if i is not None:
+                ev["plain"][i].record(s1)
+            M64.apply(xd, y64, stream=s1)
+            if i is not None:
+                ev_end["plain"][i].record(s1)
+                ev["split"][i].record(s1)
+            SP.apply(xd, ys, s_compute=s1, s_comm=s2)
+            if i is not None:
+                ev_end["split"][i].record(s1)
+                ev["f32"][i].record(s1)
+            M32.apply(x32, y32, stream=s1)
+            if i is not None:
+                ev_end["f32"][i].record(s1)
+
+    for _ in range(Wm):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(s1)
+    for i in range(K):
+        step(i)
+    t_end.record(s1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = t_start.elapsed_time(t_end)
+    form_ms = {k: float(np.mean([ev[k][i].elapsed_time(ev_end[k][i]) for i in range(K)]))
+               for k in ev}
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers ---------------
+    xh = torch.as_tensor(x).pin_memory()
+    x32h = xh.float().pin_memory()
+    yh64 = torch.empty(n, dtype=torch.float64).pin_memory()
+    yhs = torch.empty(n, dtype=torch.float64).pin_memory()
+    yh32 = torch.empty(n, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        with torch.cuda.stream(s1):
+            xd.copy_(xh, non_blocking=True)
+            x32.copy_(x32h, non_blocking=True)
+            M64.apply(xd, y64, stream=s1)
+            SP.apply(xd, ys, s_compute=s1, s_comm=s2)
+            M32.apply(x32, y32, stream=s1)
+            yh64.copy_(y64, non_blocking=True)
+            yhs.copy_(ys, non_blocking=True)
+            yh32.copy_(y32, non_blocking=True)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s1)
+    for _ in range(K):
+        e2e_step()
+    e1.record(s1)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # correctness spot check of the timed outputs (sampled rows against the oracle)
+    check = spot_check(A, x, y64, ys, y32)
+
+    forms = {}
+    if rank == 0 and not args.no_forms:
+        forms = measure_forms(M64, A, x, dev, form_ms, b_plain)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    avg_plain_s = form_ms["plain"] / 1e3
+    achieved = b_plain / avg_plain_s / 1e9
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_hash"] == kernel_hash() else None
+    cpu = cpu_baseline(A, x, b_plain) if world == 1 or rank == 0 else None
+    value = b_step * K * world / (ms / 1e3) / 1e9
+    info = M64.info()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": (f"Hamiltonian-like N={n} nnz={nnz} (stand-in for HMeP): plain FP64 "
+                                f"+ split over 8 blocks (halo {total_halo}, 2 streams) + FP32-storage"),
+                   "n_rows": n, "nnz": nnz, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (matrix 657 MB vs 126 MB L2), no flush",
+                   "plan": info},
+        "gflops": flops_step * K * world / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "k_tile<256,R=1,E,2,f64> plain FP64 product",
+                     "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "frac_of_8tbs_spec": achieved / 8000.0,
+                     "algorithmic_bytes_per_launch": b_plain},
+        "forms": {"plain_f64": {"ms": form_ms["plain"], "GBs": b_plain / form_ms["plain"] / 1e6,
+                                "GFLOPs": model.flops(nnz) / form_ms["plain"] / 1e6},
+                  "split_f64": {"ms": form_ms["split"], "GBs": b_split / form_ms["split"] / 1e6,
+                                "GFLOPs": model.flops(nnz) / form_ms["split"] / 1e6,
+                                "time_vs_plain": form_ms["split"] / form_ms["plain"],
+                                "model_eq2_vs_eq1": model.split_penalty(nnz / n) + 1},
+                  "fp32_storage": {"ms": form_ms["f32"], "GBs": b_f32 / form_ms["f32"] / 1e6,
+                                   "GFLOPs": model.flops(nnz) / form_ms["f32"] / 1e6,
+                                   "time_vs_plain": form_ms["f32"] / form_ms["plain"]},
+                  **forms},
+        "paper_model": {"nnzr": nnz / n, "B_CRS_kappa0": model.b_crs(nnz / n),
+                        "achieved_bytes_per_flop_alg": b_plain / model.flops(nnz)},
+        "check": check,
+        "cpu_baseline": cpu,
+        "e2e": {"value": b_step * K * world / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * n + 4 * n, "d2h_bytes_per_step": 8 * n + 8 * n + 4 * n,
+                "ms_per_step": e2e_ms / K},
+        "gpu_launches": 5 * K,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def spot_check(A, x, y64, ys, y32):
+    import oracle
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(A.n_rows, 2000, replace=False))
+    lens = np.diff(A.row_ptr)[rows]
+    rp = np.zeros(rows.size + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1]) for r in rows])
+    ref, bound = oracle.spmv(rp.astype(np.int32), A.col_idx[idx], A.val[idx], x, with_bound=True)
+    ref32, bound32 = oracle.spmv(rp.astype(np.int32), A.col_idx[idx],
+                                 A.val[idx].astype(np.float32).astype(np.float64),
+                                 x.astype(np.float32).astype(np.float64), with_bound=True)
+    out = {}
+    for name, y, r, b, tol in (("plain", y64, ref, bound, 1e-13), ("split", ys, ref, bound, 1e-13),
+                               ("fp32", y32, ref32, bound32, 1e-6)):
+        yy = y.detach().cpu().numpy().astype(np.float64)[rows]
+        out[name] = bool(np.all(np.abs(yy - r) <= tol * b))
+    if not all(out.values()):
+        raise RuntimeError(f"bench outputs differ from the oracle: {out}")
+    return out
+
+
+def measure_forms(M64, A, x, dev, form_ms, b_plain):
+    """Block vectors on the same matrix, each timed against the plain product."""
+    import torch
+    out = {}
+    reps = 5
+    for nrhs in (4, 8, 16, 32):
+        X = torch.rand(A.n_rows, nrhs, dtype=torch.float64, device=dev) * 2 - 1
+        Y = torch.empty_like(X)
+        M64.spmm(X, Y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            M64.spmm(X, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[f"block_nrhs{nrhs}"] = {
+            "ms": ms, "GBs": model.bytes_spmm(A.n_rows, A.n_cols, A.nnz, nrhs) / ms / 1e6,
+            "GFLOPs": model.flops(A.nnz, nrhs) / ms / 1e6,
+            "time_per_rhs_vs_plain": ms / nrhs / form_ms["plain"]}
+        del X, Y
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-forms", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

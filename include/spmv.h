@@ -107,6 +107,12 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  * tuned value.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
+/* Accumulator of an FP32-storage handle: 0 = one FP64 FMA per entry (operands
+ * widened exactly), 1 = exact-product float-float accumulation on the FP32 pipe
+ * (default; relative accuracy about 2^-44 of sum |a_ij x_j|).  FP64 handles
+ * always accumulate with FP64 FMAs and ignore this setting. */
+spmv_status spmv_set_accumulator(spmv_handle h, int32_t acc);
+
 /* Plain spMVM, Listing 1 generalised: y = alpha*A*x + beta*y.
  * x: n_cols entries of type xt; y: n_rows entries of type yt.  Supported
  * (value, x, y) types: (F64, F64, F64), (F32, F32, F32), (F32, F32, F64).  FP32

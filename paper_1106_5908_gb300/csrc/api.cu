@@ -1,0 +1,1157 @@
+// C ABI of the library (include/spmv.h): handle management, validation, the
+// row-length-histogram autotuner and tile planning, the split plan, the reverse
+// pass, the batched graph launch and the CG solvers.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "spmv.h"
+#include "internal.h"
+#include "cg.h"
+
+namespace spmv {
+int64_t transpose_work_len(int32_t n_cols);
+
+bool tile_ops(int vk, int xk, int yk, int acc, int R, int E, bool indirect, bool batched,
+              TileOps *ops) {
+    if (vk == kF64) {
+        if (xk != kF64 || yk != kF64) return false;
+        return tile_ops_f64(R, E, indirect, batched, ops);
+    }
+    return tile_ops_f32(xk, yk, acc, R, E, indirect, batched, ops);
+}
+}  // namespace spmv
+
+using namespace spmv;
+
+namespace {
+
+struct TileTable {
+    TileDesc *d = nullptr;
+    int32_t n = 0;
+    int32_t n_long = 0;
+    std::vector<TileDesc> host;
+};
+
+std::vector<TileDesc> make_tiles(const int32_t *rp, int32_t n_rows, int cap, int rowcap, int mat,
+                                 int32_t *n_long) {
+    std::vector<TileDesc> t;
+    int32_t nl = 0;
+    int32_t r = 0;
+    while (r < n_rows) {
+        const int32_t k0 = rp[r];
+        if (static_cast<int64_t>(rp[r + 1]) - k0 > cap) {
+            TileDesc d{r, r + 1, k0, rp[r + 1], mat, 0, 0, 0};
+            t.push_back(d);
+            ++nl;
+            ++r;
+            continue;
+        }
+        const int32_t lim = static_cast<int32_t>(std::min<int64_t>(n_rows, static_cast<int64_t>(r) + rowcap));
+        const int64_t target = static_cast<int64_t>(k0) + cap;
+        const int32_t *it = std::upper_bound(rp + r + 1, rp + lim + 1, target,
+                                             [](int64_t v, int32_t e) { return v < e; });
+        const int32_t r1 = static_cast<int32_t>(it - rp) - 1;
+        TileDesc d{r, r1, k0, rp[r1], mat, 0, 0, 0};
+        t.push_back(d);
+        r = r1;
+    }
+    if (n_long) *n_long = nl;
+    return t;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return SPMV_ERR_CUDA;        \
+    } while (0)
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+}  // namespace
+
+struct CgWork {
+    int64_t n = 0;
+    double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float *r32 = nullptr, *d32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    double *sc = nullptr, *partials = nullptr;
+    double *host = nullptr;  // pinned scalars
+};
+
+struct spmv_matrix {
+    int32_t n_rows = 0, n_cols = 0;
+    int64_t nnz = 0;
+    int vk = kF64;
+    int device = 0;
+    bool owns_structure = true;
+    int32_t *d_rp = nullptr;
+    int32_t *d_col = nullptr;
+    void *d_val = nullptr;
+    int32_t *d_err = nullptr;
+    std::vector<int32_t> h_rp;
+    // plan
+    int family = 0;  // 0 tile, 1 row-vector
+    int E = 15;
+    int T = 8;
+    int acc32 = kAccFF;
+    std::map<std::pair<int, int>, TileTable> tables;  // (cap, rowcap) -> tiles
+    // transposed structure (built on first use)
+    bool has_T = false;
+    int32_t *d_rowT = nullptr, *d_colT = nullptr, *d_perm = nullptr;
+    std::vector<int32_t> h_rowT;
+    std::map<std::pair<int, int>, TileTable> tablesT;
+    // FP32 mirror for IR-CG
+    spmv_matrix *mirror32 = nullptr;
+    CgWork cg;
+};
+
+struct spmv_split {
+    spmv_handle A = nullptr;
+    int32_t nblocks = 0;
+    std::vector<int32_t> block_start, halo_count;
+    std::vector<int64_t> nnz_local, nnz_nonlocal;
+    std::vector<int32_t> h_halo_map;
+    int64_t total_halo = 0;
+    int32_t *d_halo_map = nullptr;
+    double *d_halo = nullptr;
+    spmv_handle Aloc = nullptr, Anl = nullptr;
+    cudaEvent_t ev_x = nullptr, ev_halo = nullptr;
+};
+
+struct spmv_batch {
+    int32_t count = 0;
+    int vk = kF64;
+    int device = 0;
+    std::vector<spmv_handle> mats;
+    TileTable tiles;
+    int E = 15;
+    int grid = 0;
+    MatRef *d_mats = nullptr;
+    std::vector<MatRef> h_mats;
+    int32_t *d_err = nullptr;
+    std::vector<const void *> cur_x;
+    std::vector<void *> cur_y;
+    double cur_alpha = 0.0, cur_beta = 0.0;
+    bool graph_valid = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+TileTable *get_table(spmv_matrix *h, int cap, int rowcap, bool transposed) {
+    auto &tabs = transposed ? h->tablesT : h->tables;
+    auto key = std::make_pair(cap, rowcap);
+    auto it = tabs.find(key);
+    if (it != tabs.end()) return &it->second;
+    TileTable tt;
+    const std::vector<int32_t> &rp = transposed ? h->h_rowT : h->h_rp;
+    const int32_t nr = transposed ? h->n_cols : h->n_rows;
+    tt.host = make_tiles(rp.data(), nr, cap, rowcap, 0, &tt.n_long);
+    tt.n = static_cast<int32_t>(tt.host.size());
+    if (dmalloc(&tt.d, tt.host.size()) != cudaSuccess) return nullptr;
+    if (!tt.host.empty() &&
+        cudaMemcpy(tt.d, tt.host.data(), sizeof(TileDesc) * tt.host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(tt.d);
+        return nullptr;
+    }
+    auto res = tabs.emplace(key, std::move(tt));
+    return &res.first->second;
+}
+
+void free_tables(std::map<std::pair<int, int>, TileTable> &tabs) {
+    for (auto &kv : tabs) cudaFree(kv.second.d);
+    tabs.clear();
+}
+
+// E values compiled for a (value, x, y, accumulator) combination, largest first.
+int pick_E(int vk, int xk, int yk, int acc, int want) {
+    const int cands[3] = {31, 15, 7};
+    TileOps ops;
+    int best = -1;
+    for (int c : cands)
+        if (tile_ops(vk, xk, yk, acc, 1, c, false, false, &ops)) {
+            if (c == want) return c;
+            if (best < 0 || std::abs(c - want) < std::abs(best - want)) best = c;
+        }
+    return best;
+}
+
+// Autotuner: from the row-length histogram choose the per-thread entry count E
+// of the tile kernel (larger E halves the FP64 work spent joining rows cut by
+// segment ends; smaller E keeps enough tiles to fill every SM), or, for
+// matrices too small to fill the GPU with tiles, the row-vector kernel with
+// threads per row from the mean row length.
+void autotune(spmv_matrix *h) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
+    int T = 1;
+    while (T < 32 && T < mean * 0.5) T <<= 1;
+    h->T = T;
+    const int xk = h->vk;
+    const int yk = h->vk;
+    const int acc = h->vk == kF32 ? h->acc32 : kAccF64;
+    h->family = 0;
+    h->E = pick_E(h->vk, xk, yk, acc, 15);
+    for (int want : {31, 15, 7}) {
+        const int e = pick_E(h->vk, xk, yk, acc, want);
+        if (e != want) continue;
+        TileOps ops;
+        if (!tile_ops(h->vk, xk, yk, acc, 1, e, false, false, &ops)) continue;
+        const TileCfg c = ops.cfg();
+        const int64_t est_tiles = std::max<int64_t>(h->nnz / c.cap, h->n_rows / c.rowcap);
+        const int limit = ops.grid_limit();
+        if (est_tiles >= 2LL * (limit > 0 ? limit : sms)) {
+            h->E = e;
+            return;
+        }
+    }
+    // too few tiles even at the smallest E: rows to lanes instead
+    TileOps ops;
+    if (tile_ops(h->vk, xk, yk, acc, 1, 7, false, false, &ops)) {
+        const TileCfg c = ops.cfg();
+        const int64_t est_tiles = std::max<int64_t>(h->nnz / c.cap, h->n_rows / c.rowcap);
+        if (est_tiles < sms) {
+            h->family = 1;
+            h->E = 7;
+            return;
+        }
+        h->E = 7;
+    }
+}
+
+spmv_status upload_matrix(spmv_matrix *h, const int32_t *row_ptr, const int32_t *col_idx,
+                          const void *val, int val_t, bool dev_ptrs, cudaStream_t s) {
+    const size_t vsz = (h->vk == kF64) ? 8 : 4;
+    const size_t nrp = static_cast<size_t>(h->n_rows) + 1 + kRowPad;
+    const size_t nent = static_cast<size_t>(h->nnz) + kEntryPad;
+    if (dmalloc(&h->d_rp, nrp) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (dmalloc(&h->d_col, nent) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (cudaMalloc(&h->d_val, nent * vsz) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (dmalloc(&h->d_err, 1) != cudaSuccess) return SPMV_ERR_ALLOC;
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), s));
+    CK(cudaMemsetAsync(h->d_rp, 0, nrp * 4, s));
+    CK(cudaMemsetAsync(h->d_col, 0, nent * 4, s));
+    CK(cudaMemsetAsync(h->d_val, 0, nent * vsz, s));
+    CK(cudaMemcpyAsync(h->d_rp, h->h_rp.data(), (static_cast<size_t>(h->n_rows) + 1) * 4,
+                       cudaMemcpyHostToDevice, s));
+    const cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (h->nnz > 0) {
+        CK(cudaMemcpyAsync(h->d_col, col_idx, static_cast<size_t>(h->nnz) * 4, kind, s));
+        if (val_t == h->vk) {
+            CK(cudaMemcpyAsync(h->d_val, val, static_cast<size_t>(h->nnz) * vsz, kind, s));
+        } else {
+            // convert on the device through a staging buffer
+            void *tmp = nullptr;
+            const size_t tsz = static_cast<size_t>(h->nnz) * (val_t == kF64 ? 8 : 4);
+            if (cudaMalloc(&tmp, tsz) != cudaSuccess) return SPMV_ERR_ALLOC;
+            cudaError_t e = cudaMemcpyAsync(tmp, val, tsz, kind, s);
+            if (e == cudaSuccess) e = launch_convert(tmp, val_t, h->d_val, h->vk, h->nnz, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(tmp);
+            if (e != cudaSuccess) return SPMV_ERR_CUDA;
+        }
+    }
+    (void)row_ptr;
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+void destroy_cg(CgWork &w) {
+    cudaFree(w.r64); cudaFree(w.p64); cudaFree(w.q64);
+    cudaFree(w.r32); cudaFree(w.d32); cudaFree(w.p32); cudaFree(w.q32);
+    cudaFree(w.sc); cudaFree(w.partials);
+    if (w.host) cudaFreeHost(w.host);
+    w = CgWork();
+}
+
+void destroy_matrix(spmv_matrix *h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    if (h->owns_structure) {
+        cudaFree(h->d_rp);
+        cudaFree(h->d_col);
+    }
+    cudaFree(h->d_val);
+    cudaFree(h->d_err);
+    cudaFree(h->d_rowT);
+    cudaFree(h->d_colT);
+    cudaFree(h->d_perm);
+    free_tables(h->tables);
+    free_tables(h->tablesT);
+    destroy_cg(h->cg);
+    if (h->mirror32) destroy_matrix(h->mirror32);
+    delete h;
+}
+
+spmv_status create_from_host(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                             std::vector<int32_t> &&h_rp, const int32_t *col_idx, const void *val,
+                             int val_t, int store_t, bool dev_ptrs, cudaStream_t s) {
+    spmv_matrix *h = new (std::nothrow) spmv_matrix();
+    if (!h) return SPMV_ERR_ALLOC;
+    cudaGetDevice(&h->device);
+    h->n_rows = n_rows;
+    h->n_cols = n_cols;
+    h->nnz = nnz;
+    h->vk = store_t;
+    h->h_rp = std::move(h_rp);
+    spmv_status st = upload_matrix(h, nullptr, col_idx, val, val_t, dev_ptrs, s);
+    if (st != SPMV_OK) {
+        destroy_matrix(h);
+        return st;
+    }
+    autotune(h);
+    *out = h;
+    return SPMV_OK;
+}
+
+spmv_status validate_host(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                          const int32_t *col) {
+    if (rp[0] != 0) return SPMV_ERR_INVALID_INDEX;
+    for (int32_t i = 0; i < n_rows; ++i)
+        if (rp[i + 1] < rp[i]) return SPMV_ERR_INVALID_INDEX;
+    if (rp[n_rows] != nnz) return SPMV_ERR_INVALID_INDEX;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (col[k] < 0 || col[k] >= n_cols) return SPMV_ERR_INVALID_INDEX;
+    return SPMV_OK;
+}
+
+struct TileRun {
+    TileOps ops;
+    TileTable *tt;
+    int grid;
+};
+
+// Select the compiled kernel and tile table for an apply of h with group width R.
+spmv_status prepare_run(spmv_matrix *h, int xk, int yk, int R, int E, bool transposed, TileRun *run) {
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    if (!tile_ops(h->vk, xk, yk, acc, R, E, transposed, false, &run->ops)) return SPMV_ERR_UNSUPPORTED;
+    const TileCfg c = run->ops.cfg();
+    run->tt = get_table(h, c.cap, c.rowcap, transposed);
+    if (!run->tt) return SPMV_ERR_ALLOC;
+    const int lim = run->ops.grid_limit();
+    if (lim <= 0) return SPMV_ERR_CUDA;
+    run->grid = std::min<int>(run->tt->n, lim);
+    return SPMV_OK;
+}
+
+spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, double beta, void *y,
+                       int yk, cudaStream_t s) {
+    if (h->n_rows == 0) return SPMV_OK;
+    KParams p{};
+    p.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y};
+    p.rhs_count = 1;
+    p.ldx = 1;
+    p.ldy = 1;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.err = h->d_err;
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    if (h->family == 1) {
+        return launch_rowvec(p, h->n_rows, h->vk, xk, yk, acc, h->T, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+    }
+    int E = pick_E(h->vk, xk, yk, acc, h->E);
+    if (E < 0) return SPMV_ERR_UNSUPPORTED;
+    TileRun run;
+    spmv_status st = prepare_run(h, xk, yk, 1, E, false, &run);
+    if (st != SPMV_OK) return st;
+    p.tiles = run.tt->d;
+    p.n_tiles = run.tt->n;
+    return run.ops.launch(p, run.grid, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+}
+
+spmv_status ensure_transpose(spmv_matrix *h, cudaStream_t s) {
+    if (h->has_T) return SPMV_OK;
+    const size_t nT = static_cast<size_t>(h->n_cols) + 1 + kRowPad;
+    const size_t nent = static_cast<size_t>(h->nnz) + kEntryPad;
+    if (dmalloc(&h->d_rowT, nT) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (dmalloc(&h->d_colT, nent) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (dmalloc(&h->d_perm, nent) != cudaSuccess) return SPMV_ERR_ALLOC;
+    int32_t *work = nullptr;
+    if (dmalloc(&work, static_cast<size_t>(transpose_work_len(h->n_cols))) != cudaSuccess) return SPMV_ERR_ALLOC;
+    cudaError_t e = cudaMemsetAsync(h->d_rowT, 0, nT * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_colT, 0, nent * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_perm, 0, nent * 4, s);
+    if (e == cudaSuccess)
+        e = launch_transpose(h->n_rows, h->n_cols, h->nnz, h->d_rp, h->d_col, h->d_rowT, h->d_colT,
+                             h->d_perm, work, s);
+    h->h_rowT.assign(static_cast<size_t>(h->n_cols) + 1, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->h_rowT.data(), h->d_rowT, h->h_rowT.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(work);
+    if (e != cudaSuccess) return SPMV_ERR_CUDA;
+    h->has_T = true;
+    return SPMV_OK;
+}
+
+spmv_status ensure_cg(spmv_matrix *h, bool mixed) {
+    CgWork &w = h->cg;
+    const int64_t n = h->n_rows;
+    if (w.sc == nullptr) {
+        w.n = n;
+        if (dmalloc(&w.sc, kScCount) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.partials, static_cast<size_t>(cg_partials_len())) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (cudaMallocHost(reinterpret_cast<void **>(&w.host), 8 * sizeof(double)) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.r64, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+    }
+    if (!mixed && w.p64 == nullptr) {
+        if (dmalloc(&w.p64, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.q64, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+    }
+    if (mixed && w.r32 == nullptr) {
+        if (dmalloc(&w.r32, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.d32, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.p32, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+        if (dmalloc(&w.q32, n) != cudaSuccess) return SPMV_ERR_ALLOC;
+    }
+    return SPMV_OK;
+}
+
+spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
+    if (h->vk == kF32) return SPMV_OK;
+    if (h->mirror32) return SPMV_OK;
+    spmv_matrix *m = new (std::nothrow) spmv_matrix();
+    if (!m) return SPMV_ERR_ALLOC;
+    m->device = h->device;
+    m->n_rows = h->n_rows;
+    m->n_cols = h->n_cols;
+    m->nnz = h->nnz;
+    m->vk = kF32;
+    m->owns_structure = false;
+    m->d_rp = h->d_rp;
+    m->d_col = h->d_col;
+    m->h_rp = h->h_rp;
+    const size_t nent = static_cast<size_t>(h->nnz) + kEntryPad;
+    if (cudaMalloc(&m->d_val, nent * 4) != cudaSuccess || dmalloc(&m->d_err, 1) != cudaSuccess) {
+        destroy_matrix(m);
+        return SPMV_ERR_ALLOC;
+    }
+    cudaError_t e = cudaMemsetAsync(m->d_val, 0, nent * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_err, 0, 4, s);
+    if (e == cudaSuccess) e = launch_convert(h->d_val, kF64, m->d_val, kF32, h->nnz, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        destroy_matrix(m);
+        return SPMV_ERR_CUDA;
+    }
+    autotune(m);
+    h->mirror32 = m;
+    return SPMV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spmv_status_string(spmv_status s) {
+    switch (s) {
+    case SPMV_OK: return "SPMV_OK";
+    case SPMV_ERR_INVALID_ARG: return "SPMV_ERR_INVALID_ARG: invalid argument";
+    case SPMV_ERR_INVALID_INDEX: return "SPMV_ERR_INVALID_INDEX: invalid row_ptr or column index";
+    case SPMV_ERR_CUDA: return "SPMV_ERR_CUDA: CUDA runtime or kernel error";
+    case SPMV_ERR_ALLOC: return "SPMV_ERR_ALLOC: allocation failed";
+    case SPMV_ERR_UNSUPPORTED: return "SPMV_ERR_UNSUPPORTED: combination not provided";
+    case SPMV_ERR_TIMEOUT: return "SPMV_ERR_TIMEOUT: bounded device wait gave up";
+    case SPMV_ERR_NOT_CONVERGED: return "SPMV_ERR_NOT_CONVERGED: iteration cap reached";
+    }
+    return "unknown status";
+}
+
+int32_t spmv_version(void) { return 100; }
+
+spmv_status spmv_create(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                        const int32_t *row_ptr, const int32_t *col_idx, const void *val,
+                        spmv_dtype val_t, int is_device_ptr, void *stream) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return SPMV_ERR_INVALID_ARG;
+    if (val_t != SPMV_F64 && val_t != SPMV_F32) return SPMV_ERR_INVALID_ARG;
+    if (!row_ptr || (nnz > 0 && (!col_idx || !val))) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> h_rp(static_cast<size_t>(n_rows) + 1);
+    std::vector<int32_t> h_col;
+    const int32_t *col_host = col_idx;
+    if (is_device_ptr) {
+        CK(cudaMemcpyAsync(h_rp.data(), row_ptr, h_rp.size() * 4, cudaMemcpyDeviceToHost, s));
+        h_col.resize(static_cast<size_t>(nnz));
+        if (nnz) CK(cudaMemcpyAsync(h_col.data(), col_idx, static_cast<size_t>(nnz) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        col_host = h_col.data();
+    } else {
+        std::memcpy(h_rp.data(), row_ptr, h_rp.size() * 4);
+    }
+    spmv_status st = validate_host(n_rows, n_cols, nnz, h_rp.data(), col_host);
+    if (st != SPMV_OK) return st;
+    return create_from_host(out, n_rows, n_cols, nnz, std::move(h_rp), col_idx, val, val_t, val_t,
+                            is_device_ptr != 0, s);
+}
+
+void spmv_destroy(spmv_handle h) { destroy_matrix(h); }
+
+spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *stream) {
+    if (!h || (h->nnz > 0 && !val)) return SPMV_ERR_INVALID_ARG;
+    if (t != SPMV_F64 && t != SPMV_F32) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->nnz == 0) return SPMV_OK;
+    CK(launch_convert(val, t, h->d_val, h->vk, h->nnz, s));
+    if (h->mirror32) CK(launch_convert(val, t, h->mirror32->d_val, kF32, h->nnz, s));
+    return SPMV_OK;
+}
+
+spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64_t *nnz, int32_t *plan) {
+    if (!h) return SPMV_ERR_INVALID_ARG;
+    if (n_rows) *n_rows = h->n_rows;
+    if (n_cols) *n_cols = h->n_cols;
+    if (nnz) *nnz = h->nnz;
+    if (plan) {
+        DeviceGuard g(h->device);
+        const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+        const int E = pick_E(h->vk, h->vk, h->vk, acc, h->E);
+        TileOps ops;
+        int32_t ntiles = 0, rowcap = 0, nlong = 0, threads = 0;
+        if (E > 0 && tile_ops(h->vk, h->vk, h->vk, acc, 1, E, false, false, &ops)) {
+            const TileCfg c = ops.cfg();
+            TileTable *tt = get_table(h, c.cap, c.rowcap, false);
+            if (tt) {
+                ntiles = tt->n;
+                nlong = tt->n_long;
+            }
+            rowcap = c.rowcap;
+            threads = c.threads;
+        }
+        plan[0] = h->family;
+        plan[1] = E;
+        plan[2] = threads;
+        plan[3] = ntiles;
+        plan[4] = rowcap;
+        plan[5] = h->T;
+        plan[6] = nlong;
+        plan[7] = h->vk;
+    }
+    return SPMV_OK;
+}
+
+spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
+    if (!h || nbins < 1 || !counts) return SPMV_ERR_INVALID_ARG;
+    for (int32_t b = 0; b < nbins; ++b) counts[b] = 0;
+    for (int32_t i = 0; i < h->n_rows; ++i) {
+        const int32_t len = h->h_rp[i + 1] - h->h_rp[i];
+        counts[len < nbins - 1 ? len : nbins - 1] += 1;
+    }
+    return SPMV_OK;
+}
+
+spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
+    if (!h || (family != 0 && family != 1)) return SPMV_ERR_INVALID_ARG;
+    if (family == 0) {
+        if (param != 0 && (param < 3 || param > 31 || param % 2 == 0)) return SPMV_ERR_INVALID_ARG;
+        h->family = 0;
+        if (param) h->E = param;
+    } else {
+        if (param != 0 && (param < 1 || param > 32 || (param & (param - 1)))) return SPMV_ERR_INVALID_ARG;
+        h->family = 1;
+        if (param) h->T = param;
+    }
+    return SPMV_OK;
+}
+
+spmv_status spmv_set_accumulator(spmv_handle h, int32_t acc) {
+    if (!h || (acc != 0 && acc != 1)) return SPMV_ERR_INVALID_ARG;
+    h->acc32 = (acc == 0) ? kAccF64 : kAccFF;
+    return SPMV_OK;
+}
+
+spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt, double beta,
+                       void *y, spmv_dtype yt, void *stream) {
+    if (!h) return SPMV_ERR_INVALID_ARG;
+    if ((h->n_rows > 0 && !y) || (h->n_cols > 0 && h->n_rows > 0 && !x)) return SPMV_ERR_INVALID_ARG;
+    if (h->vk == kF64 && (xt != SPMV_F64 || yt != SPMV_F64)) return SPMV_ERR_UNSUPPORTED;
+    if (h->vk == kF32 && xt != SPMV_F32) return SPMV_ERR_UNSUPPORTED;
+    if (yt != SPMV_F64 && yt != SPMV_F32) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    return apply_impl(h, alpha, x, xt, beta, y, yt, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Split form
+// ---------------------------------------------------------------------------
+
+spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nblocks,
+                              const int32_t *block_row_start, int32_t *halo_count_out) {
+    if (!out || !h || nblocks < 1) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (h->n_rows != h->n_cols) return SPMV_ERR_INVALID_ARG;
+    if (h->vk != kF64) return SPMV_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    const int32_t n = h->n_rows;
+    const int64_t nnz = h->nnz;
+    std::vector<int32_t> bs(static_cast<size_t>(nblocks) + 1);
+    if (block_row_start) {
+        for (int b = 0; b <= nblocks; ++b) bs[b] = block_row_start[b];
+        if (bs[0] != 0 || bs[nblocks] != n) return SPMV_ERR_INVALID_ARG;
+        for (int b = 0; b < nblocks; ++b)
+            if (bs[b + 1] < bs[b]) return SPMV_ERR_INVALID_ARG;
+    } else {
+        // Sect. 3.2: balanced nonzeros; block b starts at the first row whose
+        // offset is at least ceil(b*nnz/nblocks)
+        bs[0] = 0;
+        for (int b = 1; b < nblocks; ++b) {
+            const int64_t target = (static_cast<int64_t>(b) * nnz + nblocks - 1) / nblocks;
+            const int32_t *it = std::lower_bound(h->h_rp.data(), h->h_rp.data() + n, target,
+                                                 [](int32_t e, int64_t v) { return e < v; });
+            bs[b] = static_cast<int32_t>(it - h->h_rp.data());
+        }
+        bs[nblocks] = n;
+    }
+    // bring the column indices to the host for the one-time bookkeeping
+    std::vector<int32_t> col(static_cast<size_t>(nnz));
+    if (nnz) CK(cudaMemcpy(col.data(), h->d_col, static_cast<size_t>(nnz) * 4, cudaMemcpyDeviceToHost));
+    std::vector<double> val(static_cast<size_t>(nnz));
+    if (nnz) CK(cudaMemcpy(val.data(), h->d_val, static_cast<size_t>(nnz) * 8, cudaMemcpyDeviceToHost));
+
+    spmv_split *sp = new (std::nothrow) spmv_split();
+    if (!sp) return SPMV_ERR_ALLOC;
+    sp->A = h;
+    sp->nblocks = nblocks;
+    sp->block_start = bs;
+    sp->halo_count.assign(nblocks, 0);
+    sp->nnz_local.assign(nblocks, 0);
+    sp->nnz_nonlocal.assign(nblocks, 0);
+
+    std::vector<int32_t> pos(static_cast<size_t>(n) + 1, -1);
+    std::vector<int32_t> rp_loc(static_cast<size_t>(n) + 1, 0), rp_nl(static_cast<size_t>(n) + 1, 0);
+    std::vector<int32_t> col_loc, col_nl;
+    std::vector<double> val_loc, val_nl;
+    col_loc.reserve(static_cast<size_t>(nnz));
+    val_loc.reserve(static_cast<size_t>(nnz));
+    for (int b = 0; b < nblocks; ++b) {
+        const int32_t lo = bs[b], hi = bs[b + 1];
+        // mark the nonlocal columns of this block, then number them in order
+        std::vector<char> used;
+        used.assign(static_cast<size_t>(n), 0);
+        for (int32_t i = lo; i < hi; ++i)
+            for (int32_t k = h->h_rp[i]; k < h->h_rp[i + 1]; ++k) {
+                const int32_t c = col[k];
+                if (c < lo || c >= hi) used[c] = 1;
+            }
+        const int64_t off = sp->total_halo;
+        int32_t cnt = 0;
+        for (int32_t c = 0; c < n; ++c)
+            if (used[c]) {
+                pos[c] = static_cast<int32_t>(off + cnt);
+                sp->h_halo_map.push_back(c);
+                ++cnt;
+            }
+        sp->halo_count[b] = cnt;
+        sp->total_halo += cnt;
+        for (int32_t i = lo; i < hi; ++i) {
+            for (int32_t k = h->h_rp[i]; k < h->h_rp[i + 1]; ++k) {
+                const int32_t c = col[k];
+                if (c >= lo && c < hi) {
+                    col_loc.push_back(c);
+                    val_loc.push_back(val[k]);
+                } else {
+                    col_nl.push_back(pos[c]);
+                    val_nl.push_back(val[k]);
+                }
+            }
+            rp_loc[i + 1] = static_cast<int32_t>(col_loc.size());
+            rp_nl[i + 1] = static_cast<int32_t>(col_nl.size());
+        }
+        sp->nnz_local[b] = rp_loc[hi] - rp_loc[lo];
+        sp->nnz_nonlocal[b] = rp_nl[hi] - rp_nl[lo];
+    }
+    if (sp->total_halo >= (int64_t(1) << 31)) {
+        delete sp;
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = nullptr;
+    spmv_status st = create_from_host(&sp->Aloc, n, n, static_cast<int64_t>(col_loc.size()),
+                                      std::vector<int32_t>(rp_loc), col_loc.data(), val_loc.data(),
+                                      kF64, kF64, false, s);
+    if (st == SPMV_OK)
+        st = create_from_host(&sp->Anl, n, static_cast<int32_t>(sp->total_halo),
+                              static_cast<int64_t>(col_nl.size()), std::vector<int32_t>(rp_nl),
+                              col_nl.data(), val_nl.data(), kF64, kF64, false, s);
+    if (st == SPMV_OK) {
+        if (dmalloc(&sp->d_halo_map, static_cast<size_t>(sp->total_halo)) != cudaSuccess ||
+            dmalloc(&sp->d_halo, static_cast<size_t>(sp->total_halo)) != cudaSuccess)
+            st = SPMV_ERR_ALLOC;
+    }
+    if (st == SPMV_OK && sp->total_halo > 0 &&
+        cudaMemcpy(sp->d_halo_map, sp->h_halo_map.data(), static_cast<size_t>(sp->total_halo) * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        st = SPMV_ERR_CUDA;
+    if (st == SPMV_OK && (cudaEventCreateWithFlags(&sp->ev_x, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&sp->ev_halo, cudaEventDisableTiming) != cudaSuccess))
+        st = SPMV_ERR_CUDA;
+    if (st != SPMV_OK) {
+        spmv_split_destroy(sp);
+        return st;
+    }
+    // the split parts use the tile kernel with the parent's per-thread work
+    sp->Aloc->family = 0;
+    sp->Anl->family = 0;
+    if (halo_count_out)
+        for (int b = 0; b < nblocks; ++b) halo_count_out[b] = sp->halo_count[b];
+    *out = sp;
+    return SPMV_OK;
+}
+
+void spmv_split_destroy(spmv_split_handle hs) {
+    if (!hs) return;
+    DeviceGuard g(hs->A ? hs->A->device : 0);
+    cudaDeviceSynchronize();
+    destroy_matrix(hs->Aloc);
+    destroy_matrix(hs->Anl);
+    cudaFree(hs->d_halo_map);
+    cudaFree(hs->d_halo);
+    if (hs->ev_x) cudaEventDestroy(hs->ev_x);
+    if (hs->ev_halo) cudaEventDestroy(hs->ev_halo);
+    delete hs;
+}
+
+spmv_status spmv_split_get_plan(spmv_split_handle hs, int32_t *nblocks, int32_t *block_start,
+                                int32_t *halo_count, int64_t *total_halo, int32_t *halo_map,
+                                int64_t *nnz_local, int64_t *nnz_nonlocal) {
+    if (!hs) return SPMV_ERR_INVALID_ARG;
+    if (nblocks) *nblocks = hs->nblocks;
+    if (block_start) std::copy(hs->block_start.begin(), hs->block_start.end(), block_start);
+    if (halo_count) std::copy(hs->halo_count.begin(), hs->halo_count.end(), halo_count);
+    if (total_halo) *total_halo = hs->total_halo;
+    if (halo_map) std::copy(hs->h_halo_map.begin(), hs->h_halo_map.end(), halo_map);
+    if (nnz_local) std::copy(hs->nnz_local.begin(), hs->nnz_local.end(), nnz_local);
+    if (nnz_nonlocal) std::copy(hs->nnz_nonlocal.begin(), hs->nnz_nonlocal.end(), nnz_nonlocal);
+    return SPMV_OK;
+}
+
+spmv_status spmv_apply_split(spmv_split_handle hs, double alpha, const double *x, double beta,
+                             double *y, void *s_compute, void *s_comm) {
+    if (!hs) return SPMV_ERR_INVALID_ARG;
+    spmv_matrix *A = hs->A;
+    if (A->n_rows > 0 && (!x || !y)) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard g(A->device);
+    cudaStream_t sc = static_cast<cudaStream_t>(s_compute);
+    cudaStream_t sm = static_cast<cudaStream_t>(s_comm);
+    // stream 2 ("communication"): wait until x is ready, gather the halo
+    if (sm != sc) {
+        CK(cudaEventRecord(hs->ev_x, sc));
+        CK(cudaStreamWaitEvent(sm, hs->ev_x, 0));
+    }
+    CK(launch_gather(x, hs->d_halo_map, hs->d_halo, hs->total_halo, sm));
+    if (sm != sc) CK(cudaEventRecord(hs->ev_halo, sm));
+    // stream 1: local part (overlaps the gather), then the nonlocal part
+    spmv_status st = apply_impl(hs->Aloc, alpha, x, kF64, beta, y, kF64, sc);
+    if (st != SPMV_OK) return st;
+    if (sm != sc) CK(cudaStreamWaitEvent(sc, hs->ev_halo, 0));
+    if (hs->Anl->nnz > 0) st = apply_impl(hs->Anl, alpha, hs->d_halo, kF64, 1.0, y, kF64, sc);
+    return st;
+}
+
+spmv_status spmv_split_get_halo(spmv_split_handle hs, double *halo_out, void *stream) {
+    if (!hs || (!halo_out && hs->total_halo > 0)) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard g(hs->A->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (hs->total_halo > 0)
+        CK(cudaMemcpyAsync(halo_out, hs->d_halo, static_cast<size_t>(hs->total_halo) * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block vectors
+// ---------------------------------------------------------------------------
+
+spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X, double beta,
+                       void *Y, spmv_dtype vt, void *stream) {
+    if (!h || nrhs < 1 || nrhs > 64) return SPMV_ERR_INVALID_ARG;
+    if (h->n_rows > 0 && (!X || !Y)) return SPMV_ERR_INVALID_ARG;
+    if (vt != SPMV_F64 || h->vk != kF64) return SPMV_ERR_UNSUPPORTED;
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h->n_rows == 0) return SPMV_OK;
+    if (nrhs == 1) return apply_impl(h, alpha, X, kF64, beta, Y, kF64, s);
+    for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
+        const int cnt = std::min(32, nrhs - c0);
+        int R = 2;
+        while (R < cnt) R <<= 1;
+        TileRun run;
+        spmv_status st = prepare_run(h, kF64, kF64, R, 15, false, &run);
+        if (st != SPMV_OK) return st;
+        KParams p{};
+        p.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, static_cast<const double *>(X) + c0,
+                     static_cast<double *>(Y) + c0};
+        p.tiles = run.tt->d;
+        p.n_tiles = run.tt->n;
+        p.rhs_count = cnt;
+        p.ldx = nrhs;
+        p.ldy = nrhs;
+        p.alpha = alpha;
+        p.beta = beta;
+        p.err = h->d_err;
+        if (run.ops.launch(p, run.grid, s) != cudaSuccess) return SPMV_ERR_CUDA;
+    }
+    return SPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reverse pass
+// ---------------------------------------------------------------------------
+
+spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void *x, void *grad_x,
+                          void *grad_val, void *stream) {
+    if (!h) return SPMV_ERR_INVALID_ARG;
+    if (grad_x && h->n_rows > 0 && !g) return SPMV_ERR_INVALID_ARG;
+    if (grad_val && h->nnz > 0 && (!g || !x)) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (grad_x && h->n_cols > 0) {
+        spmv_status st = ensure_transpose(h, s);
+        if (st != SPMV_OK) return st;
+        TileRun run;
+        st = prepare_run(h, h->vk, h->vk, 1, 15, true, &run);
+        if (st != SPMV_OK) return st;
+        KParams p{};
+        p.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x};
+        p.tiles = run.tt->d;
+        p.n_tiles = run.tt->n;
+        p.rhs_count = 1;
+        p.ldx = 1;
+        p.ldy = 1;
+        p.alpha = alpha;
+        p.beta = 0.0;
+        p.err = h->d_err;
+        if (run.ops.launch(p, run.grid, s) != cudaSuccess) return SPMV_ERR_CUDA;
+    }
+    if (grad_val && h->nnz > 0) {
+        TileOps ops;
+        const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+        if (!tile_ops(h->vk, h->vk, h->vk, acc, 1, 15, false, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+        const TileCfg c = ops.cfg();
+        TileTable *tt = get_table(h, c.cap, c.rowcap, false);
+        if (!tt) return SPMV_ERR_ALLOC;
+        if (launch_grad_val(h->d_rp, h->d_col, tt->d, tt->n, c.cap, h->vk, g, x, alpha, grad_val, s) != cudaSuccess)
+            return SPMV_ERR_CUDA;
+    }
+    return SPMV_OK;
+}
+
+spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_idx, int32_t *perm,
+                               void *stream) {
+    if (!h) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    spmv_status st = ensure_transpose(h, s);
+    if (st != SPMV_OK) return st;
+    if (rowT_ptr) std::copy(h->h_rowT.begin(), h->h_rowT.end(), rowT_ptr);
+    if (colT_idx && h->nnz) CK(cudaMemcpyAsync(colT_idx, h->d_colT, static_cast<size_t>(h->nnz) * 4, cudaMemcpyDeviceToHost, s));
+    if (perm && h->nnz) CK(cudaMemcpyAsync(perm, h->d_perm, static_cast<size_t>(h->nnz) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch
+// ---------------------------------------------------------------------------
+
+spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spmv_handle *mats) {
+    if (!out || count < 1 || !mats) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int vk = mats[0] ? mats[0]->vk : -1;
+    for (int32_t m = 0; m < count; ++m)
+        if (!mats[m] || mats[m]->vk != vk) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(mats[0]->device);
+    spmv_batch *b = new (std::nothrow) spmv_batch();
+    if (!b) return SPMV_ERR_ALLOC;
+    b->count = count;
+    b->vk = vk;
+    b->device = mats[0]->device;
+    b->mats.assign(mats, mats + count);
+    const int acc = (vk == kF32) ? kAccFF : kAccF64;
+    TileOps ops;
+    // combined histogram: E from the batch's mean row length (15 is compiled for
+    // both storage types; rows longer than a tile go the long-row path)
+    b->E = 15;
+    if (!tile_ops(vk, vk, vk, acc, 1, b->E, false, true, &ops)) {
+        delete b;
+        return SPMV_ERR_UNSUPPORTED;
+    }
+    const TileCfg c = ops.cfg();
+    for (int32_t m = 0; m < count; ++m) {
+        int32_t nl = 0;
+        std::vector<TileDesc> t = make_tiles(mats[m]->h_rp.data(), mats[m]->n_rows, c.cap, c.rowcap, m, &nl);
+        b->tiles.host.insert(b->tiles.host.end(), t.begin(), t.end());
+        b->tiles.n_long += nl;
+    }
+    b->tiles.n = static_cast<int32_t>(b->tiles.host.size());
+    b->h_mats.resize(static_cast<size_t>(count));
+    for (int32_t m = 0; m < count; ++m)
+        b->h_mats[m] = MatRef{mats[m]->d_rp, mats[m]->d_col, mats[m]->d_val, nullptr, nullptr, nullptr};
+    b->cur_x.assign(static_cast<size_t>(count), nullptr);
+    b->cur_y.assign(static_cast<size_t>(count), nullptr);
+    spmv_status st = SPMV_OK;
+    if (dmalloc(&b->tiles.d, b->tiles.host.size()) != cudaSuccess || dmalloc(&b->d_mats, b->h_mats.size()) != cudaSuccess ||
+        dmalloc(&b->d_err, 1) != cudaSuccess)
+        st = SPMV_ERR_ALLOC;
+    if (st == SPMV_OK && b->tiles.n > 0 &&
+        cudaMemcpy(b->tiles.d, b->tiles.host.data(), sizeof(TileDesc) * b->tiles.host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = SPMV_ERR_CUDA;
+    if (st == SPMV_OK && cudaMemset(b->d_err, 0, 4) != cudaSuccess) st = SPMV_ERR_CUDA;
+    const int lim = ops.grid_limit();
+    b->grid = std::min<int>(b->tiles.n, lim);
+    if (st == SPMV_OK && lim <= 0) st = SPMV_ERR_CUDA;
+    if (st != SPMV_OK) {
+        spmv_batched_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SPMV_OK;
+}
+
+void spmv_batched_destroy(spmv_batch_handle b) {
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->tiles.d);
+    cudaFree(b->d_mats);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *const *x, double beta,
+                               void *const *y, void *stream) {
+    if (!b || !x || !y) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool changed = (alpha != b->cur_alpha || beta != b->cur_beta || !b->graph_valid);
+    bool ptrs_changed = false;
+    for (int32_t m = 0; m < b->count; ++m) {
+        if (b->mats[m]->n_rows > 0 && (!x[m] || !y[m])) return SPMV_ERR_INVALID_ARG;
+        if (x[m] != b->cur_x[m] || y[m] != b->cur_y[m]) ptrs_changed = true;
+    }
+    if (ptrs_changed) {
+        for (int32_t m = 0; m < b->count; ++m) {
+            b->cur_x[m] = x[m];
+            b->cur_y[m] = y[m];
+            b->h_mats[m].x = x[m];
+            b->h_mats[m].y = y[m];
+        }
+        CK(cudaMemcpyAsync(b->d_mats, b->h_mats.data(), sizeof(MatRef) * b->h_mats.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the host table may change before the next call
+    }
+    if (b->tiles.n == 0) return SPMV_OK;
+    const int acc = (b->vk == kF32) ? kAccFF : kAccF64;
+    TileOps ops;
+    if (!tile_ops(b->vk, b->vk, b->vk, acc, 1, b->E, false, true, &ops)) return SPMV_ERR_UNSUPPORTED;
+    if (changed) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        b->graph_valid = false;
+        KParams p{};
+        p.mats = b->d_mats;
+        p.tiles = b->tiles.d;
+        p.n_tiles = b->tiles.n;
+        p.rhs_count = 1;
+        p.ldx = 1;
+        p.ldy = 1;
+        p.alpha = alpha;
+        p.beta = beta;
+        p.err = b->d_err;
+        (void)ops.grid_limit();  // sets the kernel attributes outside the capture
+        cudaStream_t cap;
+        CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = ops.launch(p, b->grid, cap);
+            e = cudaStreamEndCapture(cap, &b->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return SPMV_ERR_CUDA;
+        b->graph_valid = true;
+        b->cur_alpha = alpha;
+        b->cur_beta = beta;
+    }
+    CK(cudaGraphLaunch(b->exec, s));
+    return SPMV_OK;
+}
+
+spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan) {
+    if (!b || !plan) return SPMV_ERR_INVALID_ARG;
+    plan[0] = b->E;
+    plan[1] = 256;
+    plan[2] = b->tiles.n;
+    plan[3] = b->grid;
+    return SPMV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG solvers
+// ---------------------------------------------------------------------------
+
+spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                    double *stats, void *stream) {
+    if (!h || !b || !x || h->n_rows != h->n_cols || h->vk != kF64 || max_iter < 0) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    spmv_status st = ensure_cg(h, false);
+    if (st != SPMV_OK) return st;
+    CgWork &w = h->cg;
+    const int64_t n = h->n_rows;
+    // x = 0, r = b, p = b, rho = b.b
+    CK(cudaMemsetAsync(x, 0, static_cast<size_t>(n) * 8, s));
+    CK(cudaMemcpyAsync(w.r64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w.p64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cg_dot(b, kF64, b, kF64, n, w.partials, w.sc, kOpStore, kScRho, s));
+    CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bb = w.host[0];
+    double rho = bb;
+    int32_t it = 0;
+    while (it < max_iter && std::sqrt(rho) > tol * std::sqrt(bb)) {
+        st = apply_impl(h, 1.0, w.p64, kF64, 0.0, w.q64, kF64, s);
+        if (st != SPMV_OK) return st;
+        CK(cg_dot(w.p64, kF64, w.q64, kF64, n, w.partials, w.sc, kOpAlpha, 0, s));
+        CK(cg_update64(x, w.r64, w.p64, w.q64, n, w.partials, w.sc, s));
+        CK(cg_direction(w.p64, w.r64, kF64, w.sc, n, s));
+        CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rho = w.host[0];
+        ++it;
+    }
+    // true residual in FP64
+    CK(cudaMemcpyAsync(w.r64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
+    st = apply_impl(h, -1.0, x, kF64, 1.0, w.r64, kF64, s);
+    if (st != SPMV_OK) return st;
+    CK(cg_dot(w.r64, kF64, w.r64, kF64, n, w.partials, w.sc, kOpStore, kScNorm, s));
+    CK(cudaMemcpyAsync(w.host, w.sc + kScNorm, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double relres = bb > 0 ? std::sqrt(w.host[0] / bb) : 0.0;
+    if (stats) {
+        stats[0] = 1;
+        stats[1] = it;
+        stats[2] = relres;
+        stats[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return (std::sqrt(rho) > tol * std::sqrt(bb)) ? SPMV_ERR_NOT_CONVERGED : SPMV_OK;
+}
+
+spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_tol,
+                       int32_t max_outer, double inner_tol, int32_t max_inner, double *stats,
+                       void *stream) {
+    if (!h || !b || !x || h->n_rows != h->n_cols || h->vk != kF64 || max_outer < 0 || max_inner < 1)
+        return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    spmv_status st = ensure_cg(h, true);
+    if (st != SPMV_OK) return st;
+    st = ensure_mirror32(h, s);
+    if (st != SPMV_OK) return st;
+    spmv_matrix *A32 = h->mirror32;
+    CgWork &w = h->cg;
+    const int64_t n = h->n_rows;
+    CK(cudaMemsetAsync(x, 0, static_cast<size_t>(n) * 8, s));
+    CK(cg_dot(b, kF64, b, kF64, n, w.partials, w.sc, kOpStore, kScNorm, s));
+    CK(cudaMemcpyAsync(w.host, w.sc + kScNorm, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bnorm = std::sqrt(w.host[0]);
+    int32_t outer = 0;
+    int64_t inner_total = 0;
+    double relres = 0.0;
+    bool converged = false;
+    for (;;) {
+        // outer (FP64): r = b - A x, ||r||
+        CK(cudaMemcpyAsync(w.r64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
+        st = apply_impl(h, -1.0, x, kF64, 1.0, w.r64, kF64, s);
+        if (st != SPMV_OK) return st;
+        CK(cg_dot(w.r64, kF64, w.r64, kF64, n, w.partials, w.sc, kOpStore, kScNorm, s));
+        CK(cudaMemcpyAsync(w.host, w.sc + kScNorm, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double rnorm = std::sqrt(w.host[0]);
+        relres = bnorm > 0 ? rnorm / bnorm : 0.0;
+        if (relres <= outer_tol) { converged = true; break; }
+        if (outer >= max_outer) break;
+        // inner (FP32 storage): CG on A d = r / ||r||
+        CK(cg_scale_to32(w.r64, w.r32, 1.0 / rnorm, n, s));
+        CK(cudaMemsetAsync(w.d32, 0, static_cast<size_t>(n) * 4, s));
+        CK(cudaMemcpyAsync(w.p32, w.r32, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice, s));
+        CK(cg_dot(w.r32, kF32, w.r32, kF32, n, w.partials, w.sc, kOpStore, kScRho, s));
+        CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double rho0 = w.host[0];
+        double rho = rho0;
+        int32_t it = 0;
+        while (it < max_inner && std::sqrt(rho) > inner_tol * std::sqrt(rho0)) {
+            st = apply_impl(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, s);
+            if (st != SPMV_OK) return st;
+            CK(cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, s));
+            CK(cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, s));
+            CK(cg_direction(w.p32, w.r32, kF32, w.sc, n, s));
+            CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rho = w.host[0];
+            ++it;
+        }
+        inner_total += it;
+        // update (FP64): x += ||r|| d
+        CK(cg_axpy_64_32(x, w.d32, rnorm, n, s));
+        ++outer;
+    }
+    if (stats) {
+        stats[0] = outer;
+        stats[1] = static_cast<double>(inner_total);
+        stats[2] = relres;
+        stats[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return converged ? SPMV_OK : SPMV_ERR_NOT_CONVERGED;
+}
+
+spmv_status spmv_check_device_error(spmv_handle h, void *stream) {
+    if (!h) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t v = 0;
+    CK(cudaMemcpyAsync(&v, h->d_err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (v != 0) {
+        CK(cudaMemsetAsync(h->d_err, 0, 4, s));
+        CK(cudaStreamSynchronize(s));
+        return SPMV_ERR_TIMEOUT;
+    }
+    return SPMV_OK;
+}
+
+}  // extern "C"

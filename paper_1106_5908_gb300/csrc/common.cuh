@@ -1,0 +1,154 @@
+// Device helpers shared by the sm_103a kernels: TMA bulk copies into shared
+// memory completed through an mbarrier, bounded waits, FP32->FP64 widening on the
+// integer pipe, and the row-sum accumulators.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace spmv {
+
+// ---------------------------------------------------------------------------
+// mbarrier + cp.async.bulk (1-D bulk copy global -> shared, no tensor map)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// Bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned) from global
+// memory into this CTA's shared memory; completion is signalled on `bar`.  The
+// streamed operand is marked evict-first in L2 so it does not displace x.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint64_t *bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` to complete.  Gives up after kWaitLimitNs of
+// wall time (or kWaitLimitIters polls) and returns false; never spins forever.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr uint32_t kWaitLimitIters = 1u << 26;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 0; it < kWaitLimitIters; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 255u && global_timer_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return false;
+}
+
+// Record a device error code in the handle's error word (first one wins).
+__device__ __forceinline__ void set_error(int32_t *err, int32_t code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 -> FP64 widening without the FP64 pipe.  On GB300 the F2F.F64.F32
+// conversion issues on the (narrow) FP64 unit, at the DFMA rate; normal numbers
+// and zeros are widened here with integer operations instead (exact: the
+// exponent is rebiased by 1023-127 and the 23-bit mantissa moved up 29 bits).
+// Subnormals, infinities and NaNs fall back to the hardware conversion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t a = u & 0x7fffffffu;
+    if (a != 0u && (a - 0x00800000u) >= 0x7f000000u) return static_cast<double>(f);
+    const uint32_t hi = (u & 0x80000000u) | (a ? ((a >> 3) + 0x38000000u) : 0u);
+    const uint32_t lo = u << 29;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+template <typename T> __device__ __forceinline__ T narrow(double d);
+template <> __device__ __forceinline__ double narrow<double>(double d) { return d; }
+template <> __device__ __forceinline__ float narrow<float>(double d) { return __double2float_rn(d); }
+
+// ---------------------------------------------------------------------------
+// Row-sum accumulators.  Each holds a partial row sum and supports:
+//   zero(), fma(v, x) (acc += v*x), add(other), get() -> double.
+// ---------------------------------------------------------------------------
+
+// FP64 accumulation: exactly one DFMA per stored entry.
+struct AccF64 {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    template <typename V, typename X>
+    __device__ __forceinline__ void fma(V v, X x) { s = ::fma(widen(v), widen(x), s); }
+    __device__ __forceinline__ void add(const AccF64 &o) { s += o.s; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// Float-float accumulation on the FP32 pipe for FP32-stored operands: the product
+// of two floats is split exactly into hi + lo (FMA residual), and the running sum
+// is a normalised pair (hi, lo) updated by Knuth's two-sum.  Relative accuracy is
+// about 2^-44 of sum |a_ij x_j|, far inside the FP32-storage tolerance, while
+// using no FP64 instructions per entry.
+struct AccFF {
+    float h, l;
+    __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }
+    __device__ __forceinline__ void add_pair(float ph, float pl) {
+        const float s = h + ph;
+        const float bb = s - h;
+        float e = (h - (s - bb)) + (ph - bb);
+        e += l + pl;
+        h = s + e;
+        l = e - (h - s);
+    }
+    __device__ __forceinline__ void fma(float v, float x) {
+        const float ph = v * x;
+        const float pl = fmaf(v, x, -ph);
+        add_pair(ph, pl);
+    }
+    __device__ __forceinline__ void add(const AccFF &o) { add_pair(o.h, o.l); }
+    __device__ __forceinline__ double get() const { return widen(h) + widen(l); }
+};
+
+template <typename V, typename X> __device__ __forceinline__ X ldg_x(const X *p) { return __ldg(p); }
+
+}  // namespace spmv

@@ -1,0 +1,100 @@
+// Internal declarations shared by the translation units of the library (not part
+// of the public ABI in include/spmv.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spmv {
+
+// A tile is a run of whole rows [r0, r1) whose entries [k0, k1) are staged in
+// shared memory together.  A tile with one row and more entries than a tile
+// holds ("long row") is reduced by the whole CTA straight from global memory.
+// mat indexes the matrix table of a batched launch (0 otherwise).
+struct alignas(32) TileDesc {
+    int32_t r0, r1, k0, k1;
+    int32_t mat, pad0, pad1, pad2;
+};
+
+// Operands of one matrix.  The tile kernel streams two per-entry arrays through
+// shared memory: `col` (the gather index into x) and `vs` (the values, or, for
+// the transposed apply, the permutation into `vind` that holds the values).
+struct MatRef {
+    const int32_t *rp;    // row_ptr, padded (see kRowPad)
+    const int32_t *col;   // per-entry gather index, padded (see kEntryPad)
+    const void *vs;       // per-entry values (VT) or permutation (int32)
+    const void *vind;     // values read through the permutation, or nullptr
+    const void *x;        // dense input, element (j, r) at x[j*ldx + r]
+    void *y;              // dense output, element (i, r) at y[i*ldy + r]
+};
+
+struct KParams {
+    MatRef m;                 // the matrix of a single launch
+    const MatRef *mats;       // per-matrix table of a batched launch
+    const TileDesc *tiles;
+    int32_t n_tiles;
+    int32_t rhs_count;        // right-hand sides handled by this launch (<= group width)
+    int64_t ldx, ldy;
+    double alpha, beta;
+    int32_t *err;             // device error word
+};
+
+// Arrays handed to the tile kernel are padded so the 16-byte aligned bulk copies
+// may read a few entries past the logical end.
+constexpr int kEntryPad = 16;
+constexpr int kRowPad = 16;
+
+// Device error codes written into the error word.
+constexpr int32_t kDevErrTimeout = 1;
+
+// Kernel configuration chosen per matrix by the autotuner.
+enum ValKind : int32_t { kF64 = 0, kF32 = 1 };
+enum AccKind : int32_t { kAccF64 = 0, kAccFF = 1 };
+
+struct TileCfg {
+    int32_t E;        // entries per thread segment (odd)
+    int32_t threads;  // CTA size
+    int32_t rowcap;   // rows per tile cap
+    int32_t cap;      // entries per tile = (threads / group) * E
+};
+
+// One compiled configuration of the tile kernel.
+struct TileOps {
+    cudaError_t (*launch)(const KParams &, int grid, cudaStream_t);
+    int (*grid_limit)();   // CTAs resident on the whole GPU (persistent grid)
+    TileCfg (*cfg)();
+};
+
+// Look up a compiled configuration.  vk/xk/yk: value and vector kinds, acc:
+// accumulator, R: group width (1 for a single vector, right-hand sides per group
+// for block vectors), E: entries per segment, indirect: values read through a
+// permutation (transposed apply), batched: per-tile matrix table.
+bool tile_ops(int vk, int xk, int yk, int acc, int R, int E, bool indirect, bool batched,
+              TileOps *ops);
+bool tile_ops_f64(int R, int E, bool indirect, bool batched, TileOps *ops);
+bool tile_ops_f32(int xk, int yk, int acc, int R, int E, bool indirect, bool batched,
+                  TileOps *ops);
+
+cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
+                          int T, cudaStream_t s);
+
+// Halo gather: halo[h] = x[map[h]].
+cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
+                          cudaStream_t s);
+
+// grad_val[k] = alpha * g[row(k)] * x[col[k]] over the tiles of A.
+cudaError_t launch_grad_val(const int32_t *rp, const int32_t *col, const TileDesc *tiles,
+                            int32_t n_tiles, int32_t cap, int vk, const void *g, const void *x,
+                            double alpha, void *grad_val, cudaStream_t s);
+
+// Transposed structure: counts, exclusive scan, fill, per-row ordering.
+cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                             const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
+                             int32_t *work, cudaStream_t s);
+
+// Value conversion (FP64 <-> FP32), n entries.
+cudaError_t launch_convert(const void *src, int sk, void *dst, int dk, int64_t n, cudaStream_t s);
+
+// Vector kernels of the CG solvers (see cg.cu).
+cudaError_t launch_fill(void *p, int k, double v, int64_t n, cudaStream_t s);
+
+}  // namespace spmv

@@ -1,0 +1,391 @@
+// Auxiliary kernels: the row-vector CRS kernel (T lanes per row, shuffle
+// reduction), the halo gather of the split form, the per-entry gradient of the
+// reverse pass, the on-device transposed-CRS build and value conversions.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace spmv {
+
+// ---------------------------------------------------------------------------
+// Row-vector kernel: T consecutive lanes share one row of Listing 1, each lane
+// running an FMA chain over every T-th entry, then a butterfly shuffle reduce.
+// Used for matrices whose rows are long and uniform, and as the tuner's
+// alternative to the tile kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ AccF64 shfl_xor_acc(const AccF64 &a, int o, unsigned mask) {
+    AccF64 b;
+    b.s = __shfl_xor_sync(mask, a.s, o);
+    return b;
+}
+__device__ __forceinline__ AccFF shfl_xor_acc(const AccFF &a, int o, unsigned mask) {
+    AccFF b;
+    b.h = __shfl_xor_sync(mask, a.h, o);
+    b.l = __shfl_xor_sync(mask, a.l, o);
+    return b;
+}
+
+template <int T, typename VT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256) k_rowvec(const KParams p, int32_t n_rows) {
+    const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t row = gt / T;
+    const int lane = threadIdx.x % T;
+    const unsigned base = (threadIdx.x & 31u) & ~static_cast<unsigned>(T - 1);
+    const unsigned mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << base);
+    if (row >= n_rows) return;  // whole T-lane groups leave together
+    const int32_t *rp = p.m.rp;
+    const int32_t *col = p.m.col;
+    const VT *val = static_cast<const VT *>(p.m.vs);
+    const XT *x = static_cast<const XT *>(p.m.x);
+    YT *y = static_cast<YT *>(p.m.y);
+    ACC acc;
+    acc.zero();
+    const int kb = __ldg(rp + row), ke = __ldg(rp + row + 1);
+    for (int k = kb + lane; k < ke; k += T) acc.fma(__ldg(val + k), __ldg(x + __ldg(col + k)));
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) acc.add(shfl_xor_acc(acc, o, mask));
+    if (lane == 0) {
+        const double v = acc.get();
+        double out;
+        if (p.alpha == 1.0 && p.beta == 0.0) out = v;
+        else if (p.beta == 0.0) out = p.alpha * v;
+        else out = fma(p.alpha, v, p.beta * widen(y[row]));
+        y[row] = narrow<YT>(out);
+    }
+}
+
+template <int T, typename VT, typename XT, typename YT, typename ACC>
+static cudaError_t rowvec_launch(const KParams &p, int32_t n_rows, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const int64_t threads = static_cast<int64_t>(n_rows) * T;
+    const int grid = static_cast<int>((threads + 255) / 256);
+    k_rowvec<T, VT, XT, YT, ACC><<<grid, 256, 0, s>>>(p, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
+                          int T, cudaStream_t s) {
+#define SPMV_RV(T_)                                                                       \
+    if (T == T_) {                                                                        \
+        if (vk == kF64 && xk == kF64 && yk == kF64)                                       \
+            return rowvec_launch<T_, double, double, double, AccF64>(p, n_rows, s);       \
+        if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF)                      \
+            return rowvec_launch<T_, float, float, float, AccFF>(p, n_rows, s);           \
+        if (vk == kF32 && xk == kF32 && yk == kF64 && acc == kAccFF)                      \
+            return rowvec_launch<T_, float, float, double, AccFF>(p, n_rows, s);          \
+        if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccF64)                     \
+            return rowvec_launch<T_, float, float, float, AccF64>(p, n_rows, s);          \
+        if (vk == kF32 && xk == kF32 && yk == kF64 && acc == kAccF64)                     \
+            return rowvec_launch<T_, float, float, double, AccF64>(p, n_rows, s);         \
+        return cudaErrorInvalidValue;                                                     \
+    }
+    SPMV_RV(1)
+    SPMV_RV(2)
+    SPMV_RV(4)
+    SPMV_RV(8)
+    SPMV_RV(16)
+    SPMV_RV(32)
+#undef SPMV_RV
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Halo gather (the stand-in for the MPI exchange of Sect. 3.1-3.5): every
+// nonlocal column a block needs is copied into the contiguous halo buffer.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather(const double *__restrict__ x,
+                                                const int32_t *__restrict__ map,
+                                                double *__restrict__ halo, int64_t n) {
+    for (int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; h < n;
+         h += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        halo[h] = __ldg(x + __ldg(map + h));
+}
+
+cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
+                          cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (n + 255) / 256;
+    int grid = static_cast<int>(want < 8LL * sms ? want : 8LL * sms);
+    k_gather<<<grid, 256, 0, s>>>(x, map, halo, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// grad_val[k] = alpha * g[row(k)] * x[col[k]].  One CTA per tile of A; each
+// thread owns E consecutive entries of a chunk (row tracked as in the tile
+// kernel, alpha*g[row] formed once per row), results are staged in shared
+// memory and written out contiguously.
+// ---------------------------------------------------------------------------
+template <typename VT>
+__global__ void __launch_bounds__(256) k_grad_val(const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ col,
+                                                  const TileDesc *__restrict__ tiles,
+                                                  const VT *__restrict__ g,
+                                                  const VT *__restrict__ x, double alpha,
+                                                  VT *__restrict__ gv) {
+    constexpr int NT = 256, E = 15, CH = NT * E;
+    __shared__ VT s_out[CH];
+    __shared__ int32_t s_col[CH];
+    const TileDesc d = tiles[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int cb = d.k0; cb < d.k1; cb += CH) {
+        const int n = min(CH, d.k1 - cb);
+        for (int j = tid; j < n; j += NT) s_col[j] = __ldg(col + cb + j);
+        __syncthreads();
+        const int jb = tid * E;
+        if (jb < n) {
+            const int kb = cb + jb;
+            const int ke = min(kb + E, d.k1);
+            int lo = d.r0, hi = d.r1 - 1;  // largest row with row_ptr[row] <= kb
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(rp + mid) <= kb) lo = mid;
+                else hi = mid - 1;
+            }
+            int row = lo;
+            int next = __ldg(rp + row + 1);
+            VT scale = static_cast<VT>(static_cast<VT>(alpha) * __ldg(g + row));
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = kb + e;
+                if (k < ke) {
+                    while (k >= next) {
+                        ++row;
+                        next = __ldg(rp + row + 1);
+                        scale = static_cast<VT>(static_cast<VT>(alpha) * __ldg(g + row));
+                    }
+                    s_out[jb + e] = scale * __ldg(x + s_col[jb + e]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < n; j += NT) gv[cb + j] = s_out[j];
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_grad_val(const int32_t *rp, const int32_t *col, const TileDesc *tiles,
+                            int32_t n_tiles, int32_t cap, int vk, const void *g, const void *x,
+                            double alpha, void *grad_val, cudaStream_t s) {
+    (void)cap;
+    if (n_tiles <= 0) return cudaSuccess;
+    if (vk == kF64)
+        k_grad_val<double><<<n_tiles, 256, 0, s>>>(rp, col, tiles, static_cast<const double *>(g),
+                                                   static_cast<const double *>(x), alpha,
+                                                   static_cast<double *>(grad_val));
+    else
+        k_grad_val<float><<<n_tiles, 256, 0, s>>>(rp, col, tiles, static_cast<const float *>(g),
+                                                  static_cast<const float *>(x), alpha,
+                                                  static_cast<float *>(grad_val));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Transposed CRS on the device: count entries per column, exclusive scan,
+// scatter each entry to its column (atomic cursor), then order every row of A^T
+// by original position.  The result is independent of the atomic order.
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(const int32_t *__restrict__ col, int64_t nnz, int32_t *cnt) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nnz;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(cnt + __ldg(col + k), 1);
+}
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t *out_excl, int32_t *s_warp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int32_t wv = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+        int32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = wi - wv;  // exclusive warp offsets
+        if (lane == 31) s_warp[32] = wi;                            // block total
+    }
+    __syncthreads();
+    *out_excl = s_warp[w] + inc - v;
+    const int32_t total = s_warp[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partial(const int32_t *__restrict__ in,
+                                                               int64_t n, int32_t *sums) {
+    __shared__ int32_t s_warp[33];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanChunk;
+    int32_t v = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + static_cast<int64_t>(i) * kScanThreads + threadIdx.x;
+        if (j < n) v += in[j];
+    }
+    int32_t ex;
+    const int32_t tot = block_exclusive_scan(v, &ex, s_warp);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums in place (one block, sequential per thread).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int32_t *sums, int32_t nb) {
+    __shared__ int32_t s_warp[33];
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per;
+    int32_t v = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < nb) v += sums[b0 + i];
+    int32_t ex;
+    block_exclusive_scan(v, &ex, s_warp);
+    int32_t run = ex;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < nb) {
+            const int32_t t = sums[b0 + i];
+            sums[b0 + i] = run;
+            run += t;
+        }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t *__restrict__ in,
+                                                             int64_t n,
+                                                             const int32_t *__restrict__ offs,
+                                                             int32_t *__restrict__ out) {
+    __shared__ int32_t s_warp[33];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanChunk +
+                         static_cast<int64_t>(threadIdx.x) * kScanItems;
+    int32_t loc[kScanItems];
+    int32_t v = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        loc[i] = (j < n) ? in[j] : 0;
+        v += loc[i];
+    }
+    int32_t ex;
+    const int32_t tot = block_exclusive_scan(v, &ex, s_warp);
+    int32_t run = offs[blockIdx.x] + ex;
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t j = base + i;
+        if (j < n) out[j] = run;
+        run += loc[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offs[blockIdx.x] + tot;
+}
+
+__global__ void k_fill_transpose(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 int32_t n_rows, int32_t *cursor, int32_t *colT, int32_t *perm) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_rows;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int kb = rp[i], ke = rp[i + 1];
+        for (int k = kb; k < ke; ++k) {
+            const int pos = atomicAdd(cursor + col[k], 1);
+            colT[pos] = static_cast<int32_t>(i);
+            perm[pos] = k;
+        }
+    }
+}
+
+// Insertion sort of each row of A^T by original position (rows of A^T are short
+// for the stencil and Hamiltonian-like patterns; cost is quadratic in row length).
+__global__ void k_sort_rowsT(const int32_t *__restrict__ rowT, int32_t n_cols, int32_t *colT,
+                             int32_t *perm) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n_cols;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int b = rowT[j], e = rowT[j + 1];
+        for (int u = b + 1; u < e; ++u) {
+            const int32_t pk = perm[u], ck = colT[u];
+            int v = u - 1;
+            while (v >= b && perm[v] > pk) {
+                perm[v + 1] = perm[v];
+                colT[v + 1] = colT[v];
+                --v;
+            }
+            perm[v + 1] = pk;
+            colT[v + 1] = ck;
+        }
+    }
+}
+
+cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                             const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
+                             int32_t *work, cudaStream_t s) {
+    // work: n_cols + 1 counts/cursors followed by the scan block sums
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (static_cast<size_t>(n_cols) + 1), s);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) {
+        k_count_cols<<<8 * sms, 256, 0, s>>>(col, nnz, work);
+    }
+    const int64_t nb = (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk;
+    int32_t *sums = work + n_cols + 1;
+    if (n_cols > 0) {
+        k_scan_partial<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums);
+        k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, static_cast<int32_t>(nb));
+        k_scan_final<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums, rowT);
+    } else {
+        e = cudaMemsetAsync(rowT, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (nnz > 0) {
+        e = cudaMemcpyAsync(work, rowT, sizeof(int32_t) * static_cast<size_t>(n_cols),
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        k_fill_transpose<<<4 * sms, 256, 0, s>>>(rp, col, n_rows, work, colT, perm);
+        k_sort_rowsT<<<4 * sms, 256, 0, s>>>(rowT, n_cols, colT, perm);
+    }
+    return cudaGetLastError();
+}
+
+// Work-array length (int32 entries) launch_transpose needs.
+int64_t transpose_work_len(int32_t n_cols) {
+    return static_cast<int64_t>(n_cols) + 1 + (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Conversions and fills.
+// ---------------------------------------------------------------------------
+__global__ void k_f64_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        b[i] = __double2float_rn(a[i]);
+}
+__global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        b[i] = widen(a[i]);
+}
+
+cudaError_t launch_convert(const void *src, int sk, void *dst, int dk, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 16LL * sms));
+    if (sk == kF64 && dk == kF32)
+        k_f64_to_f32<<<grid, 256, 0, s>>>(static_cast<const double *>(src), static_cast<float *>(dst), n);
+    else if (sk == kF32 && dk == kF64)
+        k_f32_to_f64<<<grid, 256, 0, s>>>(static_cast<const float *>(src), static_cast<double *>(dst), n);
+    else if (sk == dk)
+        return cudaMemcpyAsync(dst, src, n * (sk == kF64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace spmv

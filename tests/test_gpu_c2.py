@@ -1,0 +1,131 @@
+"""GPU parity on the Hamiltonian-like matrix at full size (N = 4,194,304): plain
+FP64, the local/nonlocal split over 8 nonzero-balanced blocks (plan and halo
+bit-exact, result within tolerance, on one and on two streams), FP32 storage, and
+block vectors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_5908_gb300 import workloads as W
+from gpu_util import assert_bitexact, assert_within, dev, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def c2():
+    need_gpu()
+    A = W.hamiltonian_like(W.C2_N, seed=W.SEED_C2_MATRIX)
+    x = W.uniform(A.n_rows, W.SEED_C2_X)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    return A, x, ref, bound
+
+
+@pytest.fixture(scope="module")
+def m2(c2):
+    from paper_1106_5908_gb300 import Matrix
+    A = c2[0]
+    return Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+
+
+def test_c2_shape(c2):
+    A = c2[0]
+    assert A.n_rows == 4194304
+    assert 12.5 < A.nnz / A.n_rows < 13.5
+
+
+def test_c2_plain_f64(c2, m2):
+    A, x, ref, bound = c2
+    y = m2.apply(dev(x))
+    assert_within(host(y), ref, bound, 1e-13, "C2 plain")
+    # alpha/beta update on the same launch shape
+    y0 = W.uniform(A.n_rows, 77)
+    ref2, bound2 = oracle.spmv(*A.astuple(), x, -2.0, 0.5, y0, with_bound=True)
+    y = dev(y0)
+    m2.apply(dev(x), y, -2.0, 0.5)
+    assert_within(host(y), ref2, bound2, 1e-13, "C2 alpha/beta")
+
+
+@pytest.mark.parametrize("E", [7, 15, 31])
+def test_c2_plans(c2, m2, E):
+    A, x, ref, bound = c2
+    m2.set_plan(0, E)
+    try:
+        assert_within(host(m2.apply(dev(x))), ref, bound, 1e-13, f"C2 E={E}")
+    finally:
+        m2.set_plan(0, 15)
+
+
+def test_c2_split(c2, m2):
+    A, x, ref, bound = c2
+    sp = m2.split(8)
+    plan = sp.plan()
+    bs = oracle.split_blocks(A.row_ptr, 8)
+    assert_bitexact(plan["block_start"], bs, "block starts")
+    cnt, hmap, nl, nn = oracle.split_halo(A.row_ptr, A.col_idx, A.n_cols, bs)
+    assert_bitexact(plan["halo_count"], cnt, "halo counts")
+    assert_bitexact(plan["halo_map"], hmap, "halo map")
+    assert_bitexact(plan["nnz_local"], nl, "local entries")
+    assert_bitexact(plan["nnz_nonlocal"], nn, "nonlocal entries")
+    xd = dev(x)
+    s1 = torch.cuda.Stream()
+    s2 = torch.cuda.Stream()
+    for s_comm in (None, s2):  # one stream (naive overlap) and two streams
+        y = sp.apply(xd, s_compute=s1, s_comm=s_comm)
+        s1.synchronize()
+        assert_within(host(y), ref, bound, 1e-13, f"split comm={s_comm}")
+        assert_bitexact(sp.halo(), x[hmap], "gathered halo")
+    y0 = W.uniform(A.n_rows, 5)
+    ref2, bound2 = oracle.spmv(*A.astuple(), x, 0.5, -1.0, y0, with_bound=True)
+    y = dev(y0)
+    sp.apply(xd, y, 0.5, -1.0, s_compute=s1, s_comm=s2)
+    s1.synchronize()
+    assert_within(host(y), ref2, bound2, 1e-13, "split alpha/beta")
+
+
+def test_split_explicit_blocks_small():
+    from paper_1106_5908_gb300 import Matrix
+    A = W.hamiltonian_like(5000, seed=4)
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+    starts = [0, 100, 100, 2500, 4999, 5000]  # includes an empty block
+    sp = M.split(5, starts)
+    plan = sp.plan()
+    cnt, hmap, nl, nn = oracle.split_halo(A.row_ptr, A.col_idx, A.n_cols, np.array(starts, np.int32))
+    assert_bitexact(plan["halo_map"], hmap)
+    assert_bitexact(plan["halo_count"], cnt)
+    x = W.uniform(5000, 1)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    y = sp.apply(dev(x), s_comm=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    assert_within(host(y), ref, bound, 1e-13)
+
+
+@pytest.mark.parametrize("acc", ["ff", "f64"])
+def test_c2_fp32_storage(c2, acc):
+    from paper_1106_5908_gb300 import Matrix
+    A, x, _, _ = c2
+    v32 = A.val.astype(np.float32)
+    x32 = x.astype(np.float32)
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
+    M.set_accumulator(acc)
+    ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x32.astype(np.float64),
+                             with_bound=True)
+    assert_within(host(M.apply(dev(x32))), ref, bound, 1e-6, f"C2 fp32 y32 {acc}")
+    assert_within(host(M.apply(dev(x32), out_dtype=torch.float64)), ref, bound, 1e-6, f"C2 fp32 y64 {acc}")
+
+
+@pytest.mark.parametrize("nrhs", [4, 32])
+def test_c2_block_vectors(c2, m2, nrhs):
+    A, _, _, _ = c2
+    X = W.uniform(0, W.SEED_C4_X, shape=(A.n_rows, nrhs))
+    Y = host(m2.spmm(dev(X)))
+    rng = np.random.default_rng(nrhs)
+    rows = np.sort(rng.choice(A.n_rows, 4000, replace=False))
+    # oracle on the sampled rows (a sub-CRS with the same entries)
+    lens = np.diff(A.row_ptr)[rows]
+    rp = np.zeros(rows.size + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1]) for r in rows])
+    ref, bound = oracle.spmm(rp.astype(np.int32), A.col_idx[idx], A.val[idx], X, with_bound=True)
+    assert_within(Y[rows].ravel(), ref.ravel(), bound.ravel(), 1e-13, f"C2 nrhs={nrhs}")

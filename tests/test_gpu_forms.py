@@ -1,0 +1,219 @@
+"""GPU parity of the extended forms: block vectors, the reverse pass (transposed
+structure bit-exact; gradients against the oracle, central differences and torch
+autograd), the CG solvers, and the batched persistent launch."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_5908_gb300 import workloads as W
+from gpu_util import assert_bitexact, assert_within, dev, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def make(A):
+    from paper_1106_5908_gb300 import Matrix
+    return Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+
+
+# ---------------------------------------------------------------- block vectors
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 5, 8, 16, 31, 32, 33, 64])
+def test_spmm_small(nrhs):
+    A = W.random_csr(3000, 2000, seed=nrhs, max_len=40, long_rows=2, long_len=2500)
+    M = make(A)
+    X = W.uniform(0, 1, shape=(A.n_cols, nrhs))
+    Y0 = W.uniform(0, 2, shape=(A.n_rows, nrhs))
+    for alpha, beta in [(1.0, 0.0), (0.5, -1.5)]:
+        ref, bound = oracle.spmm(*A.astuple(), X, alpha, beta, Y0, with_bound=True)
+        Y = dev(Y0)
+        M.spmm(dev(X), Y, alpha, beta)
+        assert_within(host(Y).ravel(), ref.ravel(), bound.ravel(), 1e-13, f"nrhs={nrhs}")
+
+
+def test_spmm_integer_bitexact():
+    A = W.random_csr(2000, 2000, seed=3, integer=True, max_len=30)
+    M = make(A)
+    X = np.random.default_rng(1).integers(-8, 9, (2000, 8)).astype(np.float64)
+    assert_bitexact(host(M.spmm(dev(X))).ravel(), oracle.spmm(*A.astuple(), X).ravel())
+
+
+# ---------------------------------------------------------------- reverse pass
+
+@pytest.mark.parametrize("shape", [(1, 1), (50, 40), (700, 900), (4000, 3000)])
+def test_transpose_structure_bitexact(shape):
+    A = W.random_csr(*shape, seed=shape[0], max_len=30, long_rows=1, long_len=min(shape[1], 5000))
+    M = make(A)
+    rpt, cit, perm = M.transpose_structure()
+    ort, oct_, operm = oracle.transpose(A.row_ptr, A.col_idx, A.n_cols)
+    assert_bitexact(rpt, ort, "rowT_ptr")
+    assert_bitexact(cit, oct_, "colT")
+    assert_bitexact(perm, operm, "perm")
+
+
+@pytest.mark.parametrize("alpha", [1.0, -0.5])
+def test_backward_small(alpha):
+    A = W.random_csr(3000, 2500, seed=9, max_len=30, long_rows=2, long_len=4500)
+    M = make(A)
+    x = W.uniform(A.n_cols, 1)
+    g = W.uniform(A.n_rows, 2)
+    gx, gv = M.backward(dev(g), dev(x), alpha)
+    rgx, rgv, bound = oracle.backward(*A.astuple(), A.n_cols, g, x, alpha, with_bound=True)
+    assert_within(host(gx), rgx, bound, 1e-13, "grad_x")
+    if alpha == 1.0:
+        assert_bitexact(host(gv), rgv, "grad_val")
+    else:
+        assert_within(host(gv), rgv, np.abs(rgv), 2.5e-16, "grad_val")
+
+
+@pytest.fixture(scope="module")
+def c5():
+    return W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
+
+
+def test_backward_27pt_128(c5):
+    A = c5
+    assert (A.n_rows, A.nnz) == (2097152, 55742968)
+    M = make(A)
+    x = W.uniform(A.n_cols, W.SEED_C5_X)
+    g = W.uniform(A.n_rows, W.SEED_C5_G)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C5 forward")
+    gx, gv = M.backward(dev(g), dev(x))
+    rgx, rgv, gbound = oracle.backward(*A.astuple(), A.n_cols, g, x, with_bound=True)
+    assert_within(host(gx), rgx, gbound, 1e-13, "C5 grad_x")
+    assert_bitexact(host(gv), rgv, "C5 grad_val")
+
+
+def test_backward_27pt_fp32(c5):
+    from paper_1106_5908_gb300 import Matrix
+    A = c5
+    v32 = A.val.astype(np.float32)
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
+    x = W.uniform(A.n_cols, W.SEED_C5_X).astype(np.float32)
+    g = W.uniform(A.n_rows, W.SEED_C5_G).astype(np.float32)
+    gx, gv = M.backward(dev(g), dev(x))
+    rgx, rgv, gbound = oracle.backward(A.row_ptr, A.col_idx, v32.astype(np.float64), A.n_cols,
+                                       g.astype(np.float64), x.astype(np.float64), with_bound=True)
+    assert_within(host(gx), rgx, gbound, 1e-6, "C5 fp32 grad_x")
+    assert_within(host(gv), rgv, np.abs(rgv), 1e-6, "C5 fp32 grad_val")
+
+
+def test_autograd_fd_16cubed():
+    """SpMVFunction against central differences (torch.autograd.gradcheck) and
+    against the oracle's reverse pass on the 16^3 27-point instance."""
+    from paper_1106_5908_gb300 import spmv
+    A = W.stencil27(W.C5_FD_GRID, seed=W.SEED_C5_VAL)
+    M = make(A)
+    val = dev(A.val).requires_grad_(True)
+    x = dev(W.uniform(A.n_cols, W.SEED_C5_X)).requires_grad_(True)
+    g = W.uniform(A.n_rows, W.SEED_C5_G)
+    y = spmv(M, val, x, 1.25)
+    y.backward(dev(g))
+    rgx, rgv = oracle.backward(*A.astuple(), A.n_cols, g, host(x), 1.25)
+    np.testing.assert_allclose(host(x.grad), rgx, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(host(val.grad), rgv, rtol=1e-14, atol=0)
+    # central differences on a few entries of val and x (f linear: exact to rounding)
+    h = 1e-3
+    gd = dev(g)
+    rng = np.random.default_rng(0)
+    with torch.no_grad():
+        for k in rng.choice(A.nnz, 8, replace=False):
+            vp = val.detach().clone(); vp[k] += h
+            vm = val.detach().clone(); vm[k] -= h
+            fd = (torch.dot(gd, spmv(M, vp, x.detach(), 1.25) - spmv(M, vm, x.detach(), 1.25)) / (2 * h)).item()
+            assert fd == pytest.approx(float(host(val.grad)[k]), rel=1e-9, abs=1e-12)
+    small = W.stencil27(4, seed=1)
+    Ms = make(small)
+    vs = dev(small.val).requires_grad_(True)
+    xs = dev(W.uniform(small.n_cols, 2)).requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda v, xx: spmv(Ms, v, xx, 0.75), (vs, xs), eps=1e-6, atol=1e-8)
+
+
+# ---------------------------------------------------------------- solvers
+
+@pytest.mark.parametrize("grid", [24, W.C3_GRID])
+def test_ir_cg_and_cg(grid):
+    from paper_1106_5908_gb300 import cg, ir_cg
+    A = W.laplace3d(grid)
+    M = make(A)
+    b = W.uniform(A.n_rows, W.SEED_C3_B)
+    bd = dev(b)
+    x, st = ir_cg(M, bd, outer_tol=1e-12, max_outer=50, inner_tol=1e-4, max_inner=200)
+    assert st["converged"], st
+    xh = host(x)
+    r = oracle.residual(*A.astuple(), b, xh)
+    relres = np.linalg.norm(r) / np.linalg.norm(b)
+    assert relres <= 1e-12 * 1.5, (relres, st)
+    x64, st64 = cg(M, bd, tol=1e-12, max_iter=20000)
+    assert st64["converged"], st64
+    x64h = host(x64)
+    r64 = oracle.residual(*A.astuple(), b, x64h)
+    assert np.linalg.norm(r64) / np.linalg.norm(b) <= 1e-11, st64
+    lam_max = 3 * (2 + 2 * np.cos(np.pi / (grid + 1)))
+    lam_min = 3 * (2 - 2 * np.cos(np.pi / (grid + 1)))
+    cond = lam_max / lam_min
+    assert np.linalg.norm(xh - x64h) <= 2 * cond * 1e-11 * np.linalg.norm(x64h)
+
+
+def test_ir_cg_manufactured_solution():
+    from paper_1106_5908_gb300 import ir_cg
+    A = W.laplace2d(64)
+    M = make(A)
+    xs = W.uniform(A.n_rows, 123)
+    b = oracle.spmv(*A.astuple(), xs)
+    x, st = ir_cg(M, dev(b), outer_tol=1e-12)
+    assert st["converged"]
+    n = 64
+    cond = (2 + 2 * np.cos(np.pi / (n + 1))) / (2 - 2 * np.cos(np.pi / (n + 1)))
+    assert np.linalg.norm(host(x) - xs) <= cond * 1e-12 * np.linalg.norm(xs) * 2
+
+
+# ---------------------------------------------------------------- batched
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_small(dtype):
+    from paper_1106_5908_gb300 import Batch, Matrix
+    sizes = W.batch_sizes(24, seed=7, lo=50, hi=20000)
+    mats, As = [], []
+    for m, n in enumerate(sizes):
+        A = W.batch_matrix(m, int(n), seed=7)
+        v = A.val.astype(np.float32) if dtype == "f32" else A.val
+        As.append(W.CRS(A.row_ptr, A.col_idx, v, A.n_cols))
+        mats.append(Matrix.from_csr(A.row_ptr, A.col_idx, v, A.n_cols))
+    B = Batch(mats)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    rel = 1e-6 if dtype == "f32" else 1e-13
+    for rep, (alpha, beta) in enumerate([(1.0, 0.0), (1.0, 0.0), (-1.5, 0.5)]):
+        xs = [W.uniform(A.n_cols, 100 + 7 * rep + m).astype(np.float32 if dtype == "f32" else np.float64)
+              for m, A in enumerate(As)]
+        y0s = [W.uniform(A.n_rows, 300 + m).astype(np.float32 if dtype == "f32" else np.float64)
+               for m, A in enumerate(As)]
+        xd = [dev(x) for x in xs]
+        yd = [dev(y) for y in y0s]
+        B.apply(xd, yd, alpha, beta)
+        torch.cuda.synchronize()
+        for m, A in enumerate(As):
+            ref, bound = oracle.spmv(A.row_ptr, A.col_idx, A.val.astype(np.float64),
+                                     xs[m].astype(np.float64), alpha, beta,
+                                     y0s[m].astype(np.float64), with_bound=True)
+            assert yd[m].dtype == tdt
+            assert_within(host(yd[m]), ref, bound, rel, f"batch m={m} rep={rep}")
+
+
+def test_batched_integer_bitexact():
+    from paper_1106_5908_gb300 import Batch, Matrix
+    As = [W.random_csr(n, n, seed=n, integer=True, max_len=20, long_rows=1, long_len=min(n, 4000))
+          for n in (100, 3000, 5000, 17)]
+    B = Batch([Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols) for A in As])
+    xs = [W.integers(A.n_cols, A.n_rows) for A in As]
+    ys = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+    B.apply([dev(x) for x in xs], ys)
+    for A, x, y in zip(As, xs, ys):
+        assert_bitexact(host(y), oracle.spmv(*A.astuple(), x))

@@ -1,0 +1,179 @@
+"""GPU parity of the plain product y = alpha*A*x + beta*y (Listing 1) against the
+oracle, through the C ABI: irregular small matrices under every kernel plan,
+edge cases, and the full 2D 5-point (256^2) and 3D 7-point (160^3) operators."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_5908_gb300 import workloads as W
+from gpu_util import assert_bitexact, assert_within, dev, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PLANS = [(0, 7), (0, 15), (0, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+
+
+def make(A, dtype=None):
+    from paper_1106_5908_gb300 import Matrix
+    return Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=dtype)
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (7, 5), (64, 64), (300, 200), (3000, 2500), (20000, 20000)])
+@pytest.mark.parametrize("plan", PLANS)
+def test_random_plans(shape, plan):
+    A = W.random_csr(*shape, seed=shape[0] + plan[1], max_len=24)
+    M = make(A)
+    M.set_plan(*plan)
+    x = W.uniform(A.n_cols, 3)
+    y0 = W.uniform(A.n_rows, 4)
+    for alpha, beta in [(1.0, 0.0), (-0.75, 1.0), (2.0, -0.5), (0.0, 2.0)]:
+        ref, bound = oracle.spmv(*A.astuple(), x, alpha, beta, y0, with_bound=True)
+        y = dev(y0)
+        M.apply(dev(x), y, alpha, beta)
+        assert_within(host(y), ref, bound, 1e-13, f"plan {plan} a={alpha} b={beta}")
+
+
+@pytest.mark.parametrize("plan", PLANS[:3])
+@pytest.mark.parametrize("long_len", [1791, 1793, 3841, 9000, 40000])
+def test_long_rows(plan, long_len):
+    """Rows longer than a tile take the CTA-wide path; mixed with short ones."""
+    A = W.random_csr(400, 5000, seed=long_len, max_len=30, long_rows=5, long_len=long_len)
+    M = make(A)
+    M.set_plan(*plan)
+    x = W.uniform(A.n_cols, 5)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    y = M.apply(dev(x))
+    assert_within(host(y), ref, bound, 1e-13, f"long rows {long_len}")
+    info = M.info()
+    if plan[0] == 0:
+        cap = {7: 1792, 15: 3840, 31: 7936}[plan[1]]
+        assert info["long_rows"] == int((np.diff(A.row_ptr) > cap).sum())
+
+
+@pytest.mark.parametrize("plan", PLANS)
+def test_integer_bitexact(plan):
+    A = W.random_csr(5000, 4000, seed=11, integer=True, max_len=40, long_rows=2, long_len=5000)
+    M = make(A)
+    M.set_plan(*plan)
+    x = W.integers(A.n_cols, 12)
+    y0 = W.integers(A.n_rows, 13)
+    y = dev(y0)
+    M.apply(dev(x), y, 1.0, 1.0)
+    assert_bitexact(host(y), oracle.spmv(*A.astuple(), x, 1.0, 1.0, y0), f"integer {plan}")
+
+
+def test_edge_cases():
+    from paper_1106_5908_gb300 import Matrix
+    # no rows
+    M = Matrix.from_csr(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0), 5)
+    assert M.apply(dev(np.ones(5))).numel() == 0
+    # rows but no entries: y = beta*y
+    M = Matrix.from_csr(np.zeros(11, np.int32), np.zeros(0, np.int32), np.zeros(0), 4)
+    y0 = W.uniform(10, 1)
+    y = dev(y0)
+    M.apply(dev(np.ones(4)), y, 2.0, 0.5)
+    assert_bitexact(host(y), 0.5 * y0)
+    # no columns
+    M = Matrix.from_csr(np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0), 0)
+    y = M.apply(torch.zeros(0, dtype=torch.float64, device="cuda"), dev(np.full(3, 7.0)), 1.0, 1.0)
+    assert_bitexact(host(y), np.full(3, 7.0))
+    # beta == 0 does not read y
+    A = W.random_csr(500, 500, seed=2)
+    M = make(A)
+    x = W.uniform(500, 2)
+    y = dev(np.full(500, np.nan))
+    M.apply(dev(x), y, 1.5, 0.0)
+    ref, bound = oracle.spmv(*A.astuple(), x, 1.5, 0.0, with_bound=True)
+    assert np.all(np.isfinite(host(y)))
+    assert_within(host(y), ref, bound, 1e-13)
+
+
+def test_device_pointer_create_and_set_values():
+    from paper_1106_5908_gb300 import Matrix
+    A = W.random_csr(2000, 1500, seed=21)
+    M = Matrix.from_csr(dev(A.row_ptr), dev(A.col_idx), dev(A.val), A.n_cols)
+    x = W.uniform(A.n_cols, 1)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13)
+    v2 = W.uniform(A.nnz, 9)
+    M.set_values(dev(v2))
+    ref2, bound2 = oracle.spmv(A.row_ptr, A.col_idx, v2, x, with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref2, bound2, 1e-13)
+
+
+def test_histogram_matches_oracle():
+    A = W.random_csr(3000, 100, seed=5, max_len=50, long_rows=4, long_len=300)
+    M = make(A)
+    assert np.array_equal(M.histogram(64), oracle.row_histogram(A.row_ptr, 64))
+
+
+@pytest.mark.parametrize("plan", [(0, 7), (0, 15), (1, 4)])
+def test_laplace2d_256(plan):
+    A = W.laplace2d(W.C1_GRID)
+    assert (A.n_rows, A.nnz) == (65536, 326656)
+    M = make(A)
+    M.set_plan(*plan)
+    x = W.uniform(A.n_rows, W.SEED_C1_X)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C1 uniform")
+    xi = W.integers(A.n_rows, W.SEED_C1_XINT)
+    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "C1 integer")
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return W.laplace3d(W.C3_GRID)
+
+
+def test_laplace3d_160(c3):
+    A = c3
+    assert (A.n_rows, A.nnz) == (4096000, 28518400)
+    M = make(A)
+    x = W.uniform(A.n_rows, W.SEED_C3_B)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C3 FP64")
+    xi = W.integers(A.n_rows, 7)
+    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "C3 integer")
+
+
+@pytest.mark.parametrize("acc", ["ff", "f64"])
+@pytest.mark.parametrize("ydt", ["f32", "f64"])
+def test_fp32_storage_small(acc, ydt):
+    A = W.random_csr(6000, 5000, seed=17, max_len=40, long_rows=3, long_len=4500)
+    v32 = A.val.astype(np.float32)
+    x32 = W.uniform(A.n_cols, 2).astype(np.float32)
+    M = make(W.CRS(A.row_ptr, A.col_idx, v32, A.n_cols))
+    M.set_accumulator(acc)
+    yt = torch.float32 if ydt == "f32" else torch.float64
+    y0 = W.uniform(A.n_rows, 3)
+    ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x32.astype(np.float64),
+                             0.5, 1.0, y0.astype(np.float32).astype(np.float64) if ydt == "f32" else y0,
+                             with_bound=True)
+    y = dev(y0.astype(np.float32) if ydt == "f32" else y0)
+    M.apply(dev(x32), y, 0.5, 1.0)
+    assert y.dtype == yt
+    assert_within(host(y), ref, bound, 1e-6, f"fp32 storage acc={acc} y={ydt}")
+
+
+def test_fp32_storage_integer_bitexact():
+    A = W.random_csr(4000, 3000, seed=19, integer=True, max_len=30)
+    M = make(W.CRS(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols))
+    x = W.integers(A.n_cols, 4).astype(np.float32)
+    ref = oracle.spmv(*A.astuple(), x.astype(np.float64))
+    assert_bitexact(host(M.apply(dev(x))).astype(np.float64), ref, "fp32 integer")
+    assert_bitexact(host(M.apply(dev(x), out_dtype=torch.float64)), ref, "fp32->f64 integer")
+
+
+def test_laplace3d_160_fp32(c3):
+    A = c3
+    M = make(W.CRS(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols))
+    x = W.uniform(A.n_rows, W.SEED_C3_B).astype(np.float32)
+    ref, bound = oracle.spmv(*A.astuple(), x.astype(np.float64), with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "C3 FP32")
