@@ -14,6 +14,7 @@
 #include "spmv.h"
 #include "internal.h"
 #include "cg.h"
+#include "warp_kernel.cuh"
 
 namespace spmv {
 int64_t transpose_work_len(int32_t n_cols);
@@ -66,18 +67,6 @@ std::vector<TileDesc> make_tiles(const int32_t *rp, int32_t n_rows, int cap, int
     return t;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 #define CK(call)                                             \
     do {                                                     \
         cudaError_t e__ = (call);                            \
@@ -90,6 +79,88 @@ cudaError_t dmalloc(T **p, size_t count) {
     if (count == 0) count = 1;
     return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
 }
+
+struct ChunkTable {
+    ChunkDesc *d = nullptr;
+    uint32_t *masks = nullptr;
+    int32_t *cmat = nullptr;
+    int32_t n = 0;
+    int32_t n_long = 0;
+    int32_t n_empty = 0;
+};
+
+// Cut rows into warp chunks: whole rows whose entries fit in 32*E slots from the
+// 16-byte aligned start below the first entry, at most kWarpRowCap rows; one bit
+// per slot marks the row starts.  Rows that do not fit alone become long chunks.
+void make_chunks(const int32_t *rp, int32_t n_rows, int E, int32_t mat, std::vector<ChunkDesc> &out,
+                 std::vector<uint32_t> &masks, std::vector<int32_t> *cmat, int32_t *n_long,
+                 int32_t *n_empty) {
+    const int64_t SL = 32LL * E;
+    const int MW = E;
+    int32_t r = 0;
+    while (r < n_rows) {
+        const int32_t k0 = rp[r];
+        const int32_t base = k0 & ~3;
+        const size_t mo = masks.size();
+        masks.resize(mo + MW, 0u);
+        if (cmat) cmat->push_back(mat);
+        if (static_cast<int64_t>(rp[r + 1]) - base > SL) {
+            out.push_back(ChunkDesc{k0, rp[r + 1], r, (r + 1) | kChunkLong});
+            ++*n_long;
+            ++r;
+            continue;
+        }
+        bool empty = (rp[r + 1] == rp[r]);
+        int32_t r1 = r + 1;
+        while (r1 < n_rows && r1 - r < kWarpRowCap && static_cast<int64_t>(rp[r1 + 1]) - base <= SL) {
+            empty = empty || (rp[r1 + 1] == rp[r1]);
+            ++r1;
+        }
+        out.push_back(ChunkDesc{k0, rp[r1], r, r1 | (empty ? kChunkEmpty : 0)});
+        if (empty) ++*n_empty;
+        for (int32_t q = r; q < r1; ++q)
+            if (rp[q + 1] > rp[q]) {
+                const int32_t sl = rp[q] - base;
+                masks[mo + (sl >> 5)] |= 1u << (sl & 31);
+            }
+        r = r1;
+    }
+}
+
+spmv_status upload_chunks(ChunkTable *ct, const std::vector<ChunkDesc> &d, const std::vector<uint32_t> &m,
+                          const std::vector<int32_t> *cmat) {
+    ct->n = static_cast<int32_t>(d.size());
+    if (dmalloc(&ct->d, d.size()) != cudaSuccess || dmalloc(&ct->masks, m.size()) != cudaSuccess)
+        return SPMV_ERR_ALLOC;
+    if (cmat && dmalloc(&ct->cmat, cmat->size()) != cudaSuccess) return SPMV_ERR_ALLOC;
+    if (!d.empty() && cudaMemcpy(ct->d, d.data(), sizeof(ChunkDesc) * d.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SPMV_ERR_CUDA;
+    if (!m.empty() && cudaMemcpy(ct->masks, m.data(), 4 * m.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SPMV_ERR_CUDA;
+    if (cmat && !cmat->empty() &&
+        cudaMemcpy(ct->cmat, cmat->data(), 4 * cmat->size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SPMV_ERR_CUDA;
+    return SPMV_OK;
+}
+
+void free_chunks(ChunkTable &ct) {
+    cudaFree(ct.d);
+    cudaFree(ct.masks);
+    cudaFree(ct.cmat);
+    ct = ChunkTable();
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -113,11 +184,14 @@ struct spmv_matrix {
     int32_t *d_err = nullptr;
     std::vector<int32_t> h_rp;
     // plan
-    int family = 0;  // 0 tile, 1 row-vector
-    int E = 15;
+    int family = 0;  // 0 warp chunks, 1 row-vector, 2 staged tiles
+    int E = 16;      // entries per lane (family 0) or per thread segment (family 2)
     int T = 8;
     int acc32 = kAccFF;
     std::map<std::pair<int, int>, TileTable> tables;  // (cap, rowcap) -> tiles
+    std::map<int, ChunkTable> chunks;                   // E -> warp chunks
+    std::map<int, ChunkTable> chunksT;                  // E -> warp chunks of A^T
+    int32_t *d_rmap = nullptr;                          // output row of each stored row
     // transposed structure (built on first use)
     bool has_T = false;
     int32_t *d_rowT = nullptr, *d_colT = nullptr, *d_perm = nullptr;
@@ -147,7 +221,8 @@ struct spmv_batch {
     int device = 0;
     std::vector<spmv_handle> mats;
     TileTable tiles;
-    int E = 15;
+    ChunkTable chunks;
+    int E = 16;
     int grid = 0;
     MatRef *d_mats = nullptr;
     std::vector<MatRef> h_mats;
@@ -200,49 +275,41 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
     return best;
 }
 
-// Autotuner: from the row-length histogram choose the per-thread entry count E
-// of the tile kernel (larger E halves the FP64 work spent joining rows cut by
-// segment ends; smaller E keeps enough tiles to fill every SM), or, for
-// matrices too small to fill the GPU with tiles, the row-vector kernel with
-// threads per row from the mean row length.
+// Autotuner: from the row-length histogram choose the kernel and its work per
+// lane.  The warp-chunk kernel (family 0) keeps every FP64 FMA lane busy whatever
+// the row lengths, so it is the default; its entries per lane E is 16 (chunks of
+// 512 entries) unless rows are so short that the row cap of a chunk would leave
+// slots idle, then 8.  The row-vector kernel's lanes per row T (family 1) is the
+// power of two nearest half the mean row length, used when chosen explicitly.
 void autotune(spmv_matrix *h) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
-    const int xk = h->vk;
-    const int yk = h->vk;
-    const int acc = h->vk == kF32 ? h->acc32 : kAccF64;
     h->family = 0;
-    h->E = pick_E(h->vk, xk, yk, acc, 15);
-    for (int want : {31, 15, 7}) {
-        const int e = pick_E(h->vk, xk, yk, acc, want);
-        if (e != want) continue;
-        TileOps ops;
-        if (!tile_ops(h->vk, xk, yk, acc, 1, e, false, false, &ops)) continue;
-        const TileCfg c = ops.cfg();
-        const int64_t est_tiles = std::max<int64_t>(h->nnz / c.cap, h->n_rows / c.rowcap);
-        const int limit = ops.grid_limit();
-        if (est_tiles >= 2LL * (limit > 0 ? limit : sms)) {
-            h->E = e;
-            return;
-        }
+    h->E = (mean * kWarpRowCap >= 512.0) ? 16 : 8;
+}
+
+ChunkTable *get_chunks(spmv_matrix *h, int E, bool transposed) {
+    auto &tabs = transposed ? h->chunksT : h->chunks;
+    auto it = tabs.find(E);
+    if (it != tabs.end()) return &it->second;
+    std::vector<ChunkDesc> d;
+    std::vector<uint32_t> m;
+    ChunkTable ct;
+    const std::vector<int32_t> &rp = transposed ? h->h_rowT : h->h_rp;
+    const int32_t nr = transposed ? h->n_cols : h->n_rows;
+    make_chunks(rp.data(), nr, E, 0, d, m, nullptr, &ct.n_long, &ct.n_empty);
+    if (upload_chunks(&ct, d, m, nullptr) != SPMV_OK) {
+        free_chunks(ct);
+        return nullptr;
     }
-    // too few tiles even at the smallest E: rows to lanes instead
-    TileOps ops;
-    if (tile_ops(h->vk, xk, yk, acc, 1, 7, false, false, &ops)) {
-        const TileCfg c = ops.cfg();
-        const int64_t est_tiles = std::max<int64_t>(h->nnz / c.cap, h->n_rows / c.rowcap);
-        if (est_tiles < sms) {
-            h->family = 1;
-            h->E = 7;
-            return;
-        }
-        h->E = 7;
-    }
+    return &tabs.emplace(E, ct).first->second;
+}
+
+void free_chunk_map(std::map<int, ChunkTable> &tabs) {
+    for (auto &kv : tabs) free_chunks(kv.second);
+    tabs.clear();
 }
 
 spmv_status upload_matrix(spmv_matrix *h, const int32_t *row_ptr, const int32_t *col_idx,
@@ -305,6 +372,9 @@ void destroy_matrix(spmv_matrix *h) {
     cudaFree(h->d_perm);
     free_tables(h->tables);
     free_tables(h->tablesT);
+    free_chunk_map(h->chunks);
+    free_chunk_map(h->chunksT);
+    cudaFree(h->d_rmap);
     destroy_cg(h->cg);
     if (h->mirror32) destroy_matrix(h->mirror32);
     delete h;
@@ -364,15 +434,34 @@ spmv_status prepare_run(spmv_matrix *h, int xk, int yk, int R, int E, bool trans
 spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, double beta, void *y,
                        int yk, cudaStream_t s) {
     if (h->n_rows == 0) return SPMV_OK;
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    if (h->family == 0 || h->d_rmap) {
+        int E = h->E;
+        WarpOps ops;
+        if (!warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) {
+            E = 16;
+            if (!warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+        }
+        ChunkTable *ct = get_chunks(h, E, false);
+        if (!ct) return SPMV_ERR_ALLOC;
+        WarpParams wp{};
+        wp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, h->d_rmap};
+        wp.chunks = ct->d;
+        wp.masks = ct->masks;
+        wp.n_chunks = ct->n;
+        wp.alpha = alpha;
+        wp.beta = beta;
+        wp.err = h->d_err;
+        return ops.launch(wp, ct->n, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+    }
     KParams p{};
-    p.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y};
+    p.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
     p.rhs_count = 1;
     p.ldx = 1;
     p.ldy = 1;
     p.alpha = alpha;
     p.beta = beta;
     p.err = h->d_err;
-    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     if (h->family == 1) {
         return launch_rowvec(p, h->n_rows, h->vk, xk, yk, acc, h->T, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     }
@@ -534,23 +623,34 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
     if (plan) {
         DeviceGuard g(h->device);
         const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-        const int E = pick_E(h->vk, h->vk, h->vk, acc, h->E);
-        TileOps ops;
-        int32_t ntiles = 0, rowcap = 0, nlong = 0, threads = 0;
-        if (E > 0 && tile_ops(h->vk, h->vk, h->vk, acc, 1, E, false, false, &ops)) {
-            const TileCfg c = ops.cfg();
-            TileTable *tt = get_table(h, c.cap, c.rowcap, false);
-            if (tt) {
-                ntiles = tt->n;
-                nlong = tt->n_long;
+        int32_t E = h->E, nunits = 0, rowcap = 0, nlong = 0, threads = 256;
+        if (h->family == 2) {
+            E = pick_E(h->vk, h->vk, h->vk, acc, h->E);
+            TileOps ops;
+            if (E > 0 && tile_ops(h->vk, h->vk, h->vk, acc, 1, E, false, false, &ops)) {
+                const TileCfg c = ops.cfg();
+                TileTable *tt = get_table(h, c.cap, c.rowcap, false);
+                if (tt) {
+                    nunits = tt->n;
+                    nlong = tt->n_long;
+                }
+                rowcap = c.rowcap;
+                threads = c.threads;
             }
-            rowcap = c.rowcap;
-            threads = c.threads;
+        } else {
+            WarpOps ops;
+            if (!warp_ops(h->vk, h->vk, h->vk, acc, E, false, false, &ops)) E = 16;
+            ChunkTable *ct = get_chunks(h, E, false);
+            if (ct) {
+                nunits = ct->n;
+                nlong = ct->n_long;
+            }
+            rowcap = kWarpRowCap;
         }
         plan[0] = h->family;
         plan[1] = E;
         plan[2] = threads;
-        plan[3] = ntiles;
+        plan[3] = nunits;
         plan[4] = rowcap;
         plan[5] = h->T;
         plan[6] = nlong;
@@ -570,11 +670,15 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 }
 
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
-    if (!h || (family != 0 && family != 1)) return SPMV_ERR_INVALID_ARG;
+    if (!h || family < 0 || family > 2) return SPMV_ERR_INVALID_ARG;
     if (family == 0) {
-        if (param != 0 && (param < 3 || param > 31 || param % 2 == 0)) return SPMV_ERR_INVALID_ARG;
+        if (param != 0 && param != 8 && param != 16) return SPMV_ERR_INVALID_ARG;
         h->family = 0;
-        if (param) h->E = param;
+        h->E = param ? param : 16;
+    } else if (family == 2) {
+        if (param != 0 && (param < 3 || param > 31 || param % 2 == 0)) return SPMV_ERR_INVALID_ARG;
+        h->family = 2;
+        h->E = param ? param : 15;
     } else {
         if (param != 0 && (param < 1 || param > 32 || (param & (param - 1)))) return SPMV_ERR_INVALID_ARG;
         h->family = 1;
@@ -697,10 +801,24 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
     spmv_status st = create_from_host(&sp->Aloc, n, n, static_cast<int64_t>(col_loc.size()),
                                       std::vector<int32_t>(rp_loc), col_loc.data(), val_loc.data(),
                                       kF64, kF64, false, s);
+    // the nonlocal part keeps only rows with nonlocal entries; each stored row
+    // carries the output row it updates
+    std::vector<int32_t> nl_rows, rp_c(1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        if (rp_nl[i + 1] > rp_nl[i]) {
+            nl_rows.push_back(i);
+            rp_c.push_back(rp_nl[i + 1]);
+        }
     if (st == SPMV_OK)
-        st = create_from_host(&sp->Anl, n, static_cast<int32_t>(sp->total_halo),
-                              static_cast<int64_t>(col_nl.size()), std::vector<int32_t>(rp_nl),
+        st = create_from_host(&sp->Anl, static_cast<int32_t>(nl_rows.size()), static_cast<int32_t>(sp->total_halo),
+                              static_cast<int64_t>(col_nl.size()), std::move(rp_c),
                               col_nl.data(), val_nl.data(), kF64, kF64, false, s);
+    if (st == SPMV_OK) {
+        if (dmalloc(&sp->Anl->d_rmap, nl_rows.size()) != cudaSuccess) st = SPMV_ERR_ALLOC;
+        else if (!nl_rows.empty() && cudaMemcpy(sp->Anl->d_rmap, nl_rows.data(), 4 * nl_rows.size(),
+                                                cudaMemcpyHostToDevice) != cudaSuccess)
+            st = SPMV_ERR_CUDA;
+    }
     if (st == SPMV_OK) {
         if (dmalloc(&sp->d_halo_map, static_cast<size_t>(sp->total_halo)) != cudaSuccess ||
             dmalloc(&sp->d_halo, static_cast<size_t>(sp->total_halo)) != cudaSuccess)
@@ -836,20 +954,22 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
     if (grad_x && h->n_cols > 0) {
         spmv_status st = ensure_transpose(h, s);
         if (st != SPMV_OK) return st;
-        TileRun run;
-        st = prepare_run(h, h->vk, h->vk, 1, 15, true, &run);
-        if (st != SPMV_OK) return st;
-        KParams p{};
-        p.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x};
-        p.tiles = run.tt->d;
-        p.n_tiles = run.tt->n;
-        p.rhs_count = 1;
-        p.ldx = 1;
-        p.ldy = 1;
-        p.alpha = alpha;
-        p.beta = 0.0;
-        p.err = h->d_err;
-        if (run.ops.launch(p, run.grid, s) != cudaSuccess) return SPMV_ERR_CUDA;
+        // grad_x = alpha * A^T g: warp chunks over the rows of A^T, values read
+        // through the permutation
+        WarpOps ops;
+        const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
+        if (!warp_ops(h->vk, h->vk, h->vk, acc, 16, true, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+        ChunkTable *ct = get_chunks(h, 16, true);
+        if (!ct) return SPMV_ERR_ALLOC;
+        WarpParams wp{};
+        wp.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr};
+        wp.chunks = ct->d;
+        wp.masks = ct->masks;
+        wp.n_chunks = ct->n;
+        wp.alpha = alpha;
+        wp.beta = 0.0;
+        wp.err = h->d_err;
+        if (ops.launch(wp, ct->n, s) != cudaSuccess) return SPMV_ERR_CUDA;
     }
     if (grad_val && h->nnz > 0) {
         TileOps ops;
@@ -896,38 +1016,36 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
     b->device = mats[0]->device;
     b->mats.assign(mats, mats + count);
     const int acc = (vk == kF32) ? kAccFF : kAccF64;
-    TileOps ops;
-    // combined histogram: E from the batch's mean row length (15 is compiled for
-    // both storage types; rows longer than a tile go the long-row path)
-    b->E = 15;
-    if (!tile_ops(vk, vk, vk, acc, 1, b->E, false, true, &ops)) {
+    WarpOps ops;
+    // entries per lane from the batch's combined row-length histogram (mean row
+    // length); 16 is compiled for both storage types
+    int64_t nnz = 0, rows = 0;
+    for (int32_t m = 0; m < count; ++m) {
+        nnz += mats[m]->nnz;
+        rows += mats[m]->n_rows;
+    }
+    b->E = (rows && static_cast<double>(nnz) / rows * kWarpRowCap < 512.0) ? 8 : 16;
+    if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) b->E = 16;
+    if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) {
         delete b;
         return SPMV_ERR_UNSUPPORTED;
     }
-    const TileCfg c = ops.cfg();
-    for (int32_t m = 0; m < count; ++m) {
-        int32_t nl = 0;
-        std::vector<TileDesc> t = make_tiles(mats[m]->h_rp.data(), mats[m]->n_rows, c.cap, c.rowcap, m, &nl);
-        b->tiles.host.insert(b->tiles.host.end(), t.begin(), t.end());
-        b->tiles.n_long += nl;
-    }
-    b->tiles.n = static_cast<int32_t>(b->tiles.host.size());
+    std::vector<ChunkDesc> d;
+    std::vector<uint32_t> mk;
+    std::vector<int32_t> cm;
+    for (int32_t m = 0; m < count; ++m)
+        make_chunks(mats[m]->h_rp.data(), mats[m]->n_rows, b->E, m, d, mk, &cm, &b->chunks.n_long,
+                    &b->chunks.n_empty);
     b->h_mats.resize(static_cast<size_t>(count));
     for (int32_t m = 0; m < count; ++m)
-        b->h_mats[m] = MatRef{mats[m]->d_rp, mats[m]->d_col, mats[m]->d_val, nullptr, nullptr, nullptr};
+        b->h_mats[m] = MatRef{mats[m]->d_rp, mats[m]->d_col, mats[m]->d_val, nullptr, nullptr, nullptr, nullptr};
     b->cur_x.assign(static_cast<size_t>(count), nullptr);
     b->cur_y.assign(static_cast<size_t>(count), nullptr);
-    spmv_status st = SPMV_OK;
-    if (dmalloc(&b->tiles.d, b->tiles.host.size()) != cudaSuccess || dmalloc(&b->d_mats, b->h_mats.size()) != cudaSuccess ||
-        dmalloc(&b->d_err, 1) != cudaSuccess)
+    spmv_status st = upload_chunks(&b->chunks, d, mk, &cm);
+    if (st == SPMV_OK && (dmalloc(&b->d_mats, b->h_mats.size()) != cudaSuccess || dmalloc(&b->d_err, 1) != cudaSuccess))
         st = SPMV_ERR_ALLOC;
-    if (st == SPMV_OK && b->tiles.n > 0 &&
-        cudaMemcpy(b->tiles.d, b->tiles.host.data(), sizeof(TileDesc) * b->tiles.host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-        st = SPMV_ERR_CUDA;
     if (st == SPMV_OK && cudaMemset(b->d_err, 0, 4) != cudaSuccess) st = SPMV_ERR_CUDA;
-    const int lim = ops.grid_limit();
-    b->grid = std::min<int>(b->tiles.n, lim);
-    if (st == SPMV_OK && lim <= 0) st = SPMV_ERR_CUDA;
+    b->grid = (b->chunks.n + 7) / 8;
     if (st != SPMV_OK) {
         spmv_batched_destroy(b);
         return st;
@@ -942,7 +1060,7 @@ void spmv_batched_destroy(spmv_batch_handle b) {
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    cudaFree(b->tiles.d);
+    free_chunks(b->chunks);
     cudaFree(b->d_mats);
     cudaFree(b->d_err);
     delete b;
@@ -953,7 +1071,7 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
     if (!b || !x || !y) return SPMV_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    bool changed = (alpha != b->cur_alpha || beta != b->cur_beta || !b->graph_valid);
+    const bool recapture = (alpha != b->cur_alpha || beta != b->cur_beta || !b->graph_valid);
     bool ptrs_changed = false;
     for (int32_t m = 0; m < b->count; ++m) {
         if (b->mats[m]->n_rows > 0 && (!x[m] || !y[m])) return SPMV_ERR_INVALID_ARG;
@@ -966,33 +1084,32 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
             b->h_mats[m].x = x[m];
             b->h_mats[m].y = y[m];
         }
+        // the table is read by the kernel when the graph runs; copy it in stream order
         CK(cudaMemcpyAsync(b->d_mats, b->h_mats.data(), sizeof(MatRef) * b->h_mats.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));  // the host table may change before the next call
+        CK(cudaStreamSynchronize(s));
     }
-    if (b->tiles.n == 0) return SPMV_OK;
+    if (b->chunks.n == 0) return SPMV_OK;
     const int acc = (b->vk == kF32) ? kAccFF : kAccF64;
-    TileOps ops;
-    if (!tile_ops(b->vk, b->vk, b->vk, acc, 1, b->E, false, true, &ops)) return SPMV_ERR_UNSUPPORTED;
-    if (changed) {
+    WarpOps ops;
+    if (!warp_ops(b->vk, b->vk, b->vk, acc, b->E, false, true, &ops)) return SPMV_ERR_UNSUPPORTED;
+    if (recapture) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
         b->graph_valid = false;
-        KParams p{};
+        WarpParams p{};
         p.mats = b->d_mats;
-        p.tiles = b->tiles.d;
-        p.n_tiles = b->tiles.n;
-        p.rhs_count = 1;
-        p.ldx = 1;
-        p.ldy = 1;
+        p.chunks = b->chunks.d;
+        p.masks = b->chunks.masks;
+        p.cmat = b->chunks.cmat;
+        p.n_chunks = b->chunks.n;
         p.alpha = alpha;
         p.beta = beta;
         p.err = b->d_err;
-        (void)ops.grid_limit();  // sets the kernel attributes outside the capture
         cudaStream_t cap;
         CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = ops.launch(p, b->grid, cap);
+            cudaError_t le = ops.launch(p, b->chunks.n, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
             if (le != cudaSuccess) e = le;
         }
@@ -1011,7 +1128,7 @@ spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan) {
     if (!b || !plan) return SPMV_ERR_INVALID_ARG;
     plan[0] = b->E;
     plan[1] = 256;
-    plan[2] = b->tiles.n;
+    plan[2] = b->chunks.n;
     plan[3] = b->grid;
     return SPMV_OK;
 }

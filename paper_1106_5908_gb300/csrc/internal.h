@@ -25,6 +25,7 @@ struct MatRef {
     const void *vind;     // values read through the permutation, or nullptr
     const void *x;        // dense input, element (j, r) at x[j*ldx + r]
     void *y;              // dense output, element (i, r) at y[i*ldy + r]
+    const int32_t *rmap;  // optional: output row of each stored row (nullptr = identity)
 };
 
 struct KParams {
@@ -73,6 +74,13 @@ bool tile_ops(int vk, int xk, int yk, int acc, int R, int E, bool indirect, bool
 bool tile_ops_f64(int R, int E, bool indirect, bool batched, TileOps *ops);
 bool tile_ops_f32(int xk, int yk, int acc, int R, int E, bool indirect, bool batched,
                   TileOps *ops);
+
+struct WarpParams;
+// One compiled configuration of the warp-chunk kernel (single right-hand side).
+struct WarpOps {
+    cudaError_t (*launch)(const WarpParams &, int n_chunks, cudaStream_t);
+};
+bool warp_ops(int vk, int xk, int yk, int acc, int E, bool indirect, bool batched, WarpOps *ops);
 
 cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
                           int T, cudaStream_t s);

@@ -1,0 +1,282 @@
+// The warp-chunk CRS kernel (single right-hand side).
+//
+// Listing 1 (Sect. 1.2) sums val(j)*B(col_idx(j)) over the entries of each row.
+// On GB300 the FP64 FMA rate (about 1.2 TFLOP/s) is close to what an HBM-rate
+// spMVM needs, so the kernel keeps every lane of every FP64 FMA busy and adds no
+// per-entry FP64 work, and it keeps enough loads in flight to cover HBM and L2
+// latency without shared-memory staging or CTA barriers:
+//
+//   * The matrix is cut (once, on the host) into chunks of whole rows whose
+//     entries fit in 32*E slots counted from the 16-byte aligned start below the
+//     chunk's first entry.  Each chunk carries a bitmask with one bit per slot,
+//     set where a row starts.  One warp processes one chunk.
+//   * Lane l owns the E consecutive slots [16-byte base + l*E, ... + E).  It loads
+//     its values and column indices with 128-bit loads, then issues its E x
+//     gathers before any arithmetic, so E gathers per lane are in flight.
+//   * One FMA chain per lane runs over its slots; at a set bit the running row
+//     sum is final (stored to a per-warp row buffer in shared memory) unless the
+//     row began in an earlier lane.  A row cut by lane boundaries is combined in
+//     lane order through shuffles (one FP64 add per crossing), so results are
+//     deterministic.  Finished rows leave the row buffer row-contiguously with
+//     the alpha/beta update.
+//   * Chunks that contain empty rows take a row-per-lane path; a row too long for
+//     a chunk forms its own chunk reduced by the whole warp.
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace spmv {
+
+// Chunk descriptor: rows [r0, r1), entries [k0, k1), flags in the top bits of r1.
+struct alignas(16) ChunkDesc {
+    int32_t k0, k1, r0, r1f;
+};
+constexpr int32_t kChunkLong = 1 << 30;   // one row longer than a chunk
+constexpr int32_t kChunkEmpty = 1 << 29;  // chunk contains empty rows
+constexpr int32_t kChunkRowMask = (1 << 29) - 1;
+constexpr int kWarpRowCap = 128;          // rows per chunk (per-warp row buffer)
+
+struct WarpParams {
+    MatRef m;
+    const MatRef *mats;           // batched: per-chunk matrix table (index in cmat)
+    const ChunkDesc *chunks;
+    const uint32_t *masks;        // (32*E/32) words per chunk
+    const int32_t *cmat;          // batched: matrix of each chunk
+    int32_t n_chunks;
+    double alpha, beta;
+    int32_t *err;
+};
+
+template <typename T> struct Vec4;
+template <> struct Vec4<double> { using type = double2; static constexpr int N = 2; };
+template <> struct Vec4<float> { using type = float4; static constexpr int N = 4; };
+template <> struct Vec4<int32_t> { using type = int4; static constexpr int N = 4; };
+
+// Load E consecutive elements starting at a 16-byte aligned address with 128-bit
+// loads; groups of 4 elements past `valid` (count from p) are not read.
+template <int E, typename T>
+__device__ __forceinline__ void load_run(const T *__restrict__ p, int valid, T (&out)[E]) {
+    using V = typename Vec4<T>::type;
+    constexpr int N = Vec4<T>::N;
+#pragma unroll
+    for (int g = 0; g < E / N; ++g) {
+        V v{};
+        if (g * N < valid) v = __ldg(reinterpret_cast<const V *>(p) + g);
+        if constexpr (N == 2) {
+            out[g * 2] = reinterpret_cast<T *>(&v)[0];
+            out[g * 2 + 1] = reinterpret_cast<T *>(&v)[1];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) out[g * 4 + q] = reinterpret_cast<T *>(&v)[q];
+        }
+    }
+}
+
+template <typename YT>
+__device__ __forceinline__ void store_row(YT *__restrict__ y, int64_t row, double v, double alpha,
+                                          double beta, bool plain, const int32_t *rmap) {
+    if (rmap) row = __ldg(rmap + row);
+    double out;
+    if (plain) out = v;
+    else if (beta == 0.0) out = alpha * v;
+    else out = fma(alpha, v, beta * widen(y[row]));
+    y[row] = narrow<YT>(out);
+}
+
+__device__ __forceinline__ AccF64 shfl_up_acc(const AccF64 &a, int d) {
+    AccF64 b;
+    b.s = __shfl_up_sync(0xffffffffu, a.s, d);
+    return b;
+}
+__device__ __forceinline__ AccFF shfl_up_acc(const AccFF &a, int d) {
+    AccFF b;
+    b.h = __shfl_up_sync(0xffffffffu, a.h, d);
+    b.l = __shfl_up_sync(0xffffffffu, a.l, d);
+    return b;
+}
+__device__ __forceinline__ AccF64 shfl_xor_acc2(const AccF64 &a, int d) {
+    AccF64 b;
+    b.s = __shfl_xor_sync(0xffffffffu, a.s, d);
+    return b;
+}
+__device__ __forceinline__ AccFF shfl_xor_acc2(const AccFF &a, int d) {
+    AccFF b;
+    b.h = __shfl_xor_sync(0xffffffffu, a.h, d);
+    b.l = __shfl_xor_sync(0xffffffffu, a.l, d);
+    return b;
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+__global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
+    static_assert(E == 8 || E == 16, "E is 8 or 16");
+    constexpr int SLOTS = 32 * E;
+    constexpr int MW = SLOTS / 32;  // mask words per chunk
+    using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
+    __shared__ double s_rows[8][kWarpRowCap];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * 8 + wib;
+    if (w >= p.n_chunks) return;
+    const ChunkDesc d = p.chunks[w];
+    MatRef m;
+    if constexpr (BATCHED) m = p.mats[p.cmat[w]];
+    else m = p.m;
+    const XT *__restrict__ x = static_cast<const XT *>(m.x);
+    YT *__restrict__ y = static_cast<YT *>(m.y);
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+    const int r0 = d.r0;
+    const int r1 = d.r1f & kChunkRowMask;
+
+    if (d.r1f & kChunkLong) {
+        // one long row: lanes stride the row, then a butterfly reduction
+        ACC acc;
+        acc.zero();
+        for (int k = d.k0 + lane; k < d.k1; k += 32) {
+            const XT xv = __ldg(x + __ldg(m.col + k));
+            if constexpr (INDIRECT)
+                acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+            else
+                acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
+        if (lane == 0) store_row(y, r0, acc.get(), alpha, beta, plain, m.rmap);
+        return;
+    }
+    if (d.r1f & kChunkEmpty) {
+        // chunk with empty rows: one row per lane
+        for (int r = r0 + lane; r < r1; r += 32) {
+            ACC acc;
+            acc.zero();
+            const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
+            for (int k = kb; k < ke; ++k) {
+                const XT xv = __ldg(x + __ldg(m.col + k));
+                if constexpr (INDIRECT)
+                    acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+                else
+                    acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+            }
+            store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
+        }
+        return;
+    }
+
+    // ---- regular chunk -----------------------------------------------------
+    const int base = d.k0 & ~3;
+    const int seg = base + lane * E;
+    const int lo = max(0, d.k0 - seg);          // first valid slot of the lane
+    const int hi = min(E, d.k1 - seg);          // one past the last valid slot
+    uint32_t mbits;
+    if constexpr (E == 16) {
+        const uint32_t word = __ldg(p.masks + w * MW + (lane >> 1));
+        mbits = (word >> ((lane & 1) * 16)) & 0xffffu;
+    } else {
+        const uint32_t word = __ldg(p.masks + w * MW + (lane >> 2));
+        mbits = (word >> ((lane & 3) * 8)) & 0xffu;
+    }
+
+    VS vv[E];
+    int32_t cc[E];
+    XT xv[E];
+    load_run<E>(static_cast<const VS *>(m.vs) + seg, hi, vv);
+    load_run<E>(m.col + seg, hi, cc);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        xv[e] = XT(0);
+        if (e >= lo && e < hi) xv[e] = __ldg(x + cc[e]);
+    }
+    VT vals[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if constexpr (INDIRECT) {
+            vals[e] = VT(0);
+            if (e >= lo && e < hi) vals[e] = __ldg(static_cast<const VT *>(m.vind) + vv[e]);
+        } else {
+            vals[e] = vv[e];
+        }
+    }
+
+    // rows: exclusive prefix over lanes of the row starts in their slots
+    const int cnt = __popc(mbits);
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += t;
+    }
+    pre -= cnt;
+    const bool active = lo < hi;
+    const bool starts_first = active && ((mbits >> lo) & 1u);
+    int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
+    const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
+
+    double *srow = s_rows[wib];
+    ACC acc;
+    acc.zero();
+    ACC pend;
+    pend.zero();
+    bool started = starts_first;
+    bool has_pend = false;
+    int pend_row = row;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (e >= lo && e < hi) {
+            if ((flush >> e) & 1u) {
+                if (started) srow[row - r0] = acc.get();
+                else { has_pend = true; pend = acc; }
+                ++row;
+                acc.zero();
+                started = true;
+            }
+            acc.fma(vals[e], xv[e]);
+        }
+    }
+    // does the lane's last row end with its slots?
+    const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
+    const bool ends = (seg + E >= d.k1) || (lane < 31 && (next_bits & 1u));
+    bool carry = false;
+    if (active) {
+        if (ends) {
+            if (started) srow[row - r0] = acc.get();
+            else { has_pend = true; pend = acc; pend_row = row; }
+        } else {
+            carry = true;
+        }
+    }
+    // rows cut by lane boundaries: add the carries of the lanes before, in order
+    const bool through = carry && !started;  // the lane's slots lie inside one row
+    ACC tot = pend;
+    int dist = 1;
+    bool need = has_pend;
+    while (__any_sync(0xffffffffu, need)) {
+        const ACC c = shfl_up_acc(acc, dist);
+        const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
+        if (need) {
+            ACC t2 = c;
+            t2.add(tot);
+            tot = t2;
+            need = cthrough;
+        }
+        ++dist;
+    }
+    if (has_pend) srow[pend_row - r0] = tot.get();
+    __syncwarp();
+    for (int i = lane; i < r1 - r0; i += 32) store_row(y, r0 + i, srow[i], alpha, beta, plain, m.rmap);
+}
+
+}  // namespace spmv
+
+namespace spmv {
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+struct WarpKernel {
+    static cudaError_t launch(const WarpParams &p, int n_chunks, cudaStream_t s) {
+        if (n_chunks <= 0) return cudaSuccess;
+        const int grid = (n_chunks + 7) / 8;
+        k_warp<E, VT, XT, YT, ACC, INDIRECT, BATCHED><<<grid, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+};
+}  // namespace spmv

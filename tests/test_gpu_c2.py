@@ -47,14 +47,14 @@ def test_c2_plain_f64(c2, m2):
     assert_within(host(y), ref2, bound2, 1e-13, "C2 alpha/beta")
 
 
-@pytest.mark.parametrize("E", [7, 15, 31])
-def test_c2_plans(c2, m2, E):
+@pytest.mark.parametrize("plan", [(0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 2)])
+def test_c2_plans(c2, m2, plan):
     A, x, ref, bound = c2
-    m2.set_plan(0, E)
+    m2.set_plan(*plan)
     try:
-        assert_within(host(m2.apply(dev(x))), ref, bound, 1e-13, f"C2 E={E}")
+        assert_within(host(m2.apply(dev(x))), ref, bound, 1e-13, f"C2 plan={plan}")
     finally:
-        m2.set_plan(0, 15)
+        m2.set_plan(0, 16)
 
 
 def test_c2_split(c2, m2):

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 7), (0, 15), (0, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+PLANS = [(0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
 
 
 def make(A, dtype=None):
@@ -40,8 +40,8 @@ def test_random_plans(shape, plan):
         assert_within(host(y), ref, bound, 1e-13, f"plan {plan} a={alpha} b={beta}")
 
 
-@pytest.mark.parametrize("plan", PLANS[:3])
-@pytest.mark.parametrize("long_len", [1791, 1793, 3841, 9000, 40000])
+@pytest.mark.parametrize("plan", PLANS[:5])
+@pytest.mark.parametrize("long_len", [253, 257, 509, 513, 1791, 1793, 3841, 9000, 40000])
 def test_long_rows(plan, long_len):
     """Rows longer than a tile take the CTA-wide path; mixed with short ones."""
     A = W.random_csr(400, 5000, seed=long_len, max_len=30, long_rows=5, long_len=long_len)
@@ -52,9 +52,14 @@ def test_long_rows(plan, long_len):
     y = M.apply(dev(x))
     assert_within(host(y), ref, bound, 1e-13, f"long rows {long_len}")
     info = M.info()
-    if plan[0] == 0:
+    if plan[0] == 2:
         cap = {7: 1792, 15: 3840, 31: 7936}[plan[1]]
         assert info["long_rows"] == int((np.diff(A.row_ptr) > cap).sum())
+    else:
+        # a row is long when it does not fit 32*E slots from the aligned start
+        slots = 32 * plan[1]
+        lens = A.row_ptr[1:].astype(np.int64) - (A.row_ptr[:-1] & ~3)
+        assert info["long_rows"] == int((lens > slots).sum())
 
 
 @pytest.mark.parametrize("plan", PLANS)
@@ -114,7 +119,7 @@ def test_histogram_matches_oracle():
     assert np.array_equal(M.histogram(64), oracle.row_histogram(A.row_ptr, 64))
 
 
-@pytest.mark.parametrize("plan", [(0, 7), (0, 15), (1, 4)])
+@pytest.mark.parametrize("plan", [(0, 16), (0, 8), (2, 15), (1, 4)])
 def test_laplace2d_256(plan):
     A = W.laplace2d(W.C1_GRID)
     assert (A.n_rows, A.nnz) == (65536, 326656)
