@@ -96,7 +96,7 @@ void make_chunks(const int32_t *rp, int32_t n_rows, int E, int32_t mat, std::vec
                  std::vector<uint32_t> &masks, std::vector<int32_t> *cmat, int32_t *n_long,
                  int32_t *n_empty) {
     const int64_t SL = 32LL * E;
-    const int MW = E;
+    const int MW = ((E + 3) / 4) * 4;  // mask words per chunk, rows of 16 bytes
     int32_t r = 0;
     while (r < n_rows) {
         const int32_t k0 = rp[r];
@@ -672,7 +672,7 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
     if (!h || family < 0 || family > 2) return SPMV_ERR_INVALID_ARG;
     if (family == 0) {
-        if (param != 0 && param != 8 && param != 16) return SPMV_ERR_INVALID_ARG;
+        if (param != 0 && param != 7 && param != 8 && param != 15 && param != 16) return SPMV_ERR_INVALID_ARG;
         h->family = 0;
         h->E = param ? param : 16;
     } else if (family == 2) {

@@ -1,0 +1,280 @@
+// The pipelined warp-chunk CRS kernel (single right-hand side).
+//
+// Same chunking, row bitmasks, per-lane FMA chains and lane-order carries as the
+// warp-chunk kernel, but each warp is persistent and streams its chunks through a
+// private two-stage shared-memory ring filled by cp.async.bulk (1-D TMA, 16-byte
+// aligned, evict-first in L2): while a warp gathers x and runs the FMA chains of
+// one chunk, the values, column indices and row bitmask of its next chunk are in
+// flight.  Warps never wait for each other (no CTA barrier); each stage has its
+// own mbarrier.  E is odd so lanes reading shared memory at stride E use
+// distinct banks.
+#pragma once
+#include <type_traits>
+
+#include "warp_kernel.cuh"
+
+namespace spmv {
+
+template <int E, typename VS>
+struct PipeLayout {
+    static constexpr int SLOTS = 32 * E;
+    static constexpr int SL = SLOTS + 8;                 // alignment slack
+    static constexpr int MWP = ((E + 3) / 4) * 4;        // mask words per chunk (16-byte rows)
+    static constexpr size_t al(size_t v) { return (v + 15) & ~size_t(15); }
+    static constexpr size_t off_vs = 0;
+    static constexpr size_t off_col = off_vs + al(sizeof(VS) * SL);
+    static constexpr size_t off_mask = off_col + al(4 * SL);
+    static constexpr size_t off_desc = off_mask + al(4 * MWP);
+    static constexpr size_t stage = off_desc + 16;
+    static constexpr size_t off_rows = 2 * stage;
+    static constexpr size_t off_bar = off_rows + 8 * kWarpRowCap;
+    static constexpr size_t warp_bytes = al(off_bar + 16);
+    static constexpr size_t block_bytes = 8 * warp_bytes;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+__global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
+    static_assert(E % 2 == 1, "odd E: conflict-free strided shared-memory reads");
+    using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
+    using L = PipeLayout<E, VS>;
+    constexpr int SLOTS = L::SLOTS;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char *ws = smem + wib * L::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L::off_bar);
+    double *srow = reinterpret_cast<double *>(ws + L::off_rows);
+    const int nwarps = gridDim.x * 8;
+    int c = blockIdx.x * 8 + wib;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (c >= p.n_chunks) return;
+
+    uint64_t policy = 0;
+    if (lane == 0) policy = l2_evict_first_policy();
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+
+    auto is_regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
+    // Lane 0: publish chunk cc's descriptor in stage s and start its copies.
+    auto issue = [&](int cc, const ChunkDesc &d, int s) {
+        unsigned char *st = ws + s * L::stage;
+        *reinterpret_cast<ChunkDesc *>(st + L::off_desc) = d;
+        if (is_regular(d)) {
+            MatRef m;
+            if constexpr (BATCHED) m = p.mats[p.cmat[cc]];
+            else m = p.m;
+            const int base = d.k0 & ~3;
+            const int n = ((d.k1 - base) + 3) & ~3;
+            const uint32_t bv = static_cast<uint32_t>(n * sizeof(VS));
+            const uint32_t bc = static_cast<uint32_t>(n * 4);
+            const uint32_t bm = static_cast<uint32_t>(L::MWP * 4);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[s], bv + bc + bm);
+            bulk_g2s(st + L::off_vs, static_cast<const VS *>(m.vs) + base, bv, &bar[s], policy);
+            bulk_g2s(st + L::off_col, m.col + base, bc, &bar[s], policy);
+            bulk_g2s(st + L::off_mask, p.masks + static_cast<int64_t>(cc) * L::MWP, bm, &bar[s], policy);
+        } else {
+            mbar_arrive(&bar[s]);
+        }
+    };
+
+    ChunkDesc dnext{};
+    if (lane == 0) {
+        const ChunkDesc d0 = p.chunks[c];
+        issue(c, d0, 0);
+        if (c + nwarps < p.n_chunks) dnext = p.chunks[c + nwarps];
+    }
+    uint32_t phase = 0;
+    for (int i = 0; c < p.n_chunks; c += nwarps, ++i) {
+        const int s = i & 1;
+        const int cn = c + nwarps;
+        if (lane == 0 && cn < p.n_chunks) {
+            issue(cn, dnext, s ^ 1);
+            if (cn + nwarps < p.n_chunks) dnext = p.chunks[cn + nwarps];
+        }
+        bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+        phase ^= 1u << s;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            if (lane == 0) {
+                set_error(p.err, kDevErrTimeout);
+                if (cn < p.n_chunks) (void)mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u);
+            }
+            return;
+        }
+        unsigned char *st = ws + s * L::stage;
+        const ChunkDesc d = *reinterpret_cast<const ChunkDesc *>(st + L::off_desc);
+        MatRef m;
+        if constexpr (BATCHED) m = p.mats[p.cmat[c]];
+        else m = p.m;
+        const XT *__restrict__ x = static_cast<const XT *>(m.x);
+        YT *__restrict__ y = static_cast<YT *>(m.y);
+        const int r0 = d.r0;
+        const int r1 = d.r1f & kChunkRowMask;
+
+        if (d.r1f & kChunkLong) {
+            ACC acc;
+            acc.zero();
+            for (int k = d.k0 + lane; k < d.k1; k += 32) {
+                const XT xv = __ldg(x + __ldg(m.col + k));
+                if constexpr (INDIRECT)
+                    acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+                else
+                    acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
+            if (lane == 0) store_row(y, r0, acc.get(), alpha, beta, plain, m.rmap);
+        } else if (d.r1f & kChunkEmpty) {
+            for (int r = r0 + lane; r < r1; r += 32) {
+                ACC acc;
+                acc.zero();
+                const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
+                for (int k = kb; k < ke; ++k) {
+                    const XT xv = __ldg(x + __ldg(m.col + k));
+                    if constexpr (INDIRECT)
+                        acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+                    else
+                        acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+                }
+                store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
+            }
+        } else {
+            const VS *sv = reinterpret_cast<const VS *>(st + L::off_vs);
+            const int32_t *sc = reinterpret_cast<const int32_t *>(st + L::off_col);
+            const uint32_t *smk = reinterpret_cast<const uint32_t *>(st + L::off_mask);
+            const int base = d.k0 & ~3;
+            const int off = lane * E;              // first slot of the lane
+            const int lo = max(0, d.k0 - base - off);
+            const int hi = min(E, d.k1 - base - off);
+            const int w0 = off >> 5, sh = off & 31;
+            const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
+            const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
+
+            XT xv[E];
+            VT vals[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                xv[e] = XT(0);
+                if (e >= lo && e < hi) xv[e] = __ldg(x + sc[off + e]);
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if constexpr (INDIRECT) {
+                    vals[e] = VT(0);
+                    if (e >= lo && e < hi) vals[e] = __ldg(static_cast<const VT *>(m.vind) + sv[off + e]);
+                } else {
+                    vals[e] = (e >= lo && e < hi) ? sv[off + e] : VT(0);
+                }
+            }
+            const int cnt = __popc(mbits);
+            int pre = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += t;
+            }
+            pre -= cnt;
+            const bool active = lo < hi;
+            const bool starts_first = active && ((mbits >> lo) & 1u);
+            int row = r0 + pre + (starts_first ? 1 : 0) - 1;
+            const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
+            ACC acc;
+            acc.zero();
+            ACC pend;
+            pend.zero();
+            bool started = starts_first;
+            bool has_pend = false;
+            int pend_row = row;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (e >= lo && e < hi) {
+                    if ((flush >> e) & 1u) {
+                        if (started) srow[row - r0] = acc.get();
+                        else { has_pend = true; pend = acc; }
+                        ++row;
+                        acc.zero();
+                        started = true;
+                    }
+                    acc.fma(vals[e], xv[e]);
+                }
+            }
+            const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
+            const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
+            bool carry = false;
+            if (active) {
+                if (ends) {
+                    if (started) srow[row - r0] = acc.get();
+                    else { has_pend = true; pend = acc; pend_row = row; }
+                } else {
+                    carry = true;
+                }
+            }
+            const bool through = carry && !started;
+            ACC tot = pend;
+            int dist = 1;
+            bool need = has_pend;
+            while (__any_sync(0xffffffffu, need)) {
+                const ACC cv = shfl_up_acc(acc, dist);
+                const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
+                if (need) {
+                    ACC t2 = cv;
+                    t2.add(tot);
+                    tot = t2;
+                    need = cthrough;
+                }
+                ++dist;
+            }
+            if (has_pend) srow[pend_row - r0] = tot.get();
+            __syncwarp();
+            for (int q = lane; q < r1 - r0; q += 32) store_row(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
+        }
+        // every lane is done with stage s (and the row buffer) before lane 0
+        // refills it at the next iteration
+        __syncwarp();
+    }
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+struct PipeKernel {
+    using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
+    using L = PipeLayout<E, VS>;
+    static constexpr auto fn = k_pipe<E, VT, XT, YT, ACC, INDIRECT, BATCHED>;
+    static int grid_limit() {
+        static int cached = -1;
+        static int cached_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cached >= 0 && cached_dev == dev) return cached;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(L::block_bytes)) != cudaSuccess)
+            return 0;
+        int per_sm = 0, sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, L::block_bytes) != cudaSuccess)
+            return 0;
+        cached = per_sm * sms;
+        cached_dev = dev;
+        return cached;
+    }
+    static cudaError_t launch(const WarpParams &p, int n_chunks, cudaStream_t s) {
+        if (n_chunks <= 0) return cudaSuccess;
+        const int lim = grid_limit();
+        if (lim <= 0) return cudaErrorInvalidConfiguration;
+        const int want = (n_chunks + 7) / 8;
+        fn<<<want < lim ? want : lim, 256, L::block_bytes, s>>>(p);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace spmv
