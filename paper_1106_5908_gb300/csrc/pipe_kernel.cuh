@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
     const int wib = threadIdx.x >> 5;
     unsigned char *ws = smem + wib * L::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L::off_bar);
-    double *srow = reinterpret_cast<double *>(ws + L::off_rows);
+    ACC *srow = reinterpret_cast<ACC *>(ws + L::off_rows);
     const int nwarps = gridDim.x * 8;
     int c = blockIdx.x * 8 + wib;
     if (lane == 0) {
@@ -123,32 +123,9 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
         const int r1 = d.r1f & kChunkRowMask;
 
         if (d.r1f & kChunkLong) {
-            ACC acc;
-            acc.zero();
-            for (int k = d.k0 + lane; k < d.k1; k += 32) {
-                const XT xv = __ldg(x + __ldg(m.col + k));
-                if constexpr (INDIRECT)
-                    acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
-                else
-                    acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
-            }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
-            if (lane == 0) store_row(y, r0, acc.get(), alpha, beta, plain, m.rmap);
+            long_row<VT, XT, YT, ACC, INDIRECT>(m, d, x, y, alpha, beta, plain, lane);
         } else if (d.r1f & kChunkEmpty) {
-            for (int r = r0 + lane; r < r1; r += 32) {
-                ACC acc;
-                acc.zero();
-                const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
-                for (int k = kb; k < ke; ++k) {
-                    const XT xv = __ldg(x + __ldg(m.col + k));
-                    if constexpr (INDIRECT)
-                        acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
-                    else
-                        acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
-                }
-                store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
-            }
+            rows_per_lane<VT, XT, YT, ACC, INDIRECT>(m, r0, r1, x, y, alpha, beta, plain, lane);
         } else {
             const VS *sv = reinterpret_cast<const VS *>(st + L::off_vs);
             const int32_t *sc = reinterpret_cast<const int32_t *>(st + L::off_col);
@@ -160,7 +137,6 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
             const int w0 = off >> 5, sh = off & 31;
             const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
             const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
-
             XT xv[E];
             VT vals[E];
 #pragma unroll
@@ -170,74 +146,18 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                if constexpr (INDIRECT) {
-                    vals[e] = VT(0);
-                    if (e >= lo && e < hi) vals[e] = __ldg(static_cast<const VT *>(m.vind) + sv[off + e]);
-                } else {
-                    vals[e] = (e >= lo && e < hi) ? sv[off + e] : VT(0);
-                }
-            }
-            const int cnt = __popc(mbits);
-            int pre = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, pre, o);
-                if (lane >= o) pre += t;
-            }
-            pre -= cnt;
-            const bool active = lo < hi;
-            const bool starts_first = active && ((mbits >> lo) & 1u);
-            int row = r0 + pre + (starts_first ? 1 : 0) - 1;
-            const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
-            ACC acc;
-            acc.zero();
-            ACC pend;
-            pend.zero();
-            bool started = starts_first;
-            bool has_pend = false;
-            int pend_row = row;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
+                vals[e] = VT(0);
                 if (e >= lo && e < hi) {
-                    if ((flush >> e) & 1u) {
-                        if (started) srow[row - r0] = acc.get();
-                        else { has_pend = true; pend = acc; }
-                        ++row;
-                        acc.zero();
-                        started = true;
-                    }
-                    acc.fma(vals[e], xv[e]);
+                    if constexpr (INDIRECT) vals[e] = __ldg(static_cast<const VT *>(m.vind) + sv[off + e]);
+                    else vals[e] = sv[off + e];
                 }
             }
             const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
             const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
-            bool carry = false;
-            if (active) {
-                if (ends) {
-                    if (started) srow[row - r0] = acc.get();
-                    else { has_pend = true; pend = acc; pend_row = row; }
-                } else {
-                    carry = true;
-                }
-            }
-            const bool through = carry && !started;
-            ACC tot = pend;
-            int dist = 1;
-            bool need = has_pend;
-            while (__any_sync(0xffffffffu, need)) {
-                const ACC cv = shfl_up_acc(acc, dist);
-                const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
-                if (need) {
-                    ACC t2 = cv;
-                    t2.add(tot);
-                    tot = t2;
-                    need = cthrough;
-                }
-                ++dist;
-            }
-            if (has_pend) srow[pend_row - r0] = tot.get();
+            chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
-            for (int q = lane; q < r1 - r0; q += 32) store_row(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
+            for (int q = lane; q < r1 - r0; q += 32)
+                store_row(y, r0 + q, srow[q].get(), alpha, beta, plain, m.rmap);
         }
         // every lane is done with stage s (and the row buffer) before lane 0
         // refills it at the next iteration

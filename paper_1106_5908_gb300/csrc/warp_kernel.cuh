@@ -107,13 +107,118 @@ __device__ __forceinline__ AccFF shfl_xor_acc2(const AccFF &a, int d) {
     return b;
 }
 
+// A row too long for a chunk: lanes stride the row, then a butterfly reduction.
+template <typename VT, typename XT, typename YT, typename ACC, bool INDIRECT>
+__device__ __forceinline__ void long_row(const MatRef &m, const ChunkDesc &d, const XT *__restrict__ x,
+                                         YT *__restrict__ y, double alpha, double beta, bool plain,
+                                         int lane) {
+    ACC acc;
+    acc.zero();
+    for (int k = d.k0 + lane; k < d.k1; k += 32) {
+        const XT xv = __ldg(x + __ldg(m.col + k));
+        if constexpr (INDIRECT)
+            acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+        else
+            acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
+    if (lane == 0) store_row(y, d.r0, acc.get(), alpha, beta, plain, m.rmap);
+}
+
+// A chunk with empty rows: one row per lane straight from global memory.
+template <typename VT, typename XT, typename YT, typename ACC, bool INDIRECT>
+__device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, const XT *__restrict__ x,
+                                              YT *__restrict__ y, double alpha, double beta, bool plain,
+                                              int lane) {
+    for (int r = r0 + lane; r < r1; r += 32) {
+        ACC acc;
+        acc.zero();
+        const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
+        for (int k = kb; k < ke; ++k) {
+            const XT xv = __ldg(x + __ldg(m.col + k));
+            if constexpr (INDIRECT)
+                acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
+            else
+                acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
+        }
+        store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
+    }
+}
+
+// One lane's share of a regular chunk.  vals/xv hold the lane's E slots (zero in
+// slots outside [lo, hi)); bit e of mbits is set where a row starts in slot e;
+// `ends` says whether the lane's last row ends with its slots.  The FMA chain
+// restarts at every row start (a register select, no branch) and the running sum
+// of the current row is stored to the row buffer after every entry once the row
+// is known to have started in this lane, so the last store of a row is its full
+// sum.  The part of the first row that started in an earlier lane is combined in
+// lane order with the carries of those lanes (one FP64 add per crossing).
+template <int E, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
+                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
+    const int cnt = __popc(mbits);
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += t;
+    }
+    pre -= cnt;  // row starts in the chunk before this lane's slots
+    const bool active = lo < hi;
+    const bool starts_first = active && ((mbits >> lo) & 1u);
+    int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
+    const int first_row = row;
+    const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
+    ACC acc;
+    acc.zero();
+    ACC pend;
+    pend.zero();
+    bool started = starts_first;
+    bool has_pend = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const bool b = (flush >> e) & 1u;
+        const bool cap = b && !started;
+        if (cap) pend = acc;
+        has_pend = has_pend || cap;
+        if (b) acc.zero();
+        row += b ? 1 : 0;
+        started = started || b;
+        acc.fma(vals[e], xv[e]);
+        if (started) srow[row - r0] = acc;
+    }
+    if (active && !started && ends) {
+        pend = acc;
+        has_pend = true;
+    }
+    const bool carry = active && !ends;
+    const bool through = carry && !started;  // the lane's slots lie inside one row
+    ACC tot = pend;
+    int dist = 1;
+    bool need = has_pend;
+    while (__any_sync(0xffffffffu, need)) {
+        const ACC c = shfl_up_acc(acc, dist);
+        const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
+        if (need) {
+            ACC t2 = c;
+            t2.add(tot);
+            tot = t2;
+            need = cthrough;
+        }
+        ++dist;
+    }
+    if (has_pend) srow[first_row - r0] = tot;
+}
+
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
 __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
     static_assert(E == 8 || E == 16, "E is 8 or 16");
     constexpr int SLOTS = 32 * E;
     constexpr int MW = SLOTS / 32;  // mask words per chunk
     using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
-    __shared__ double s_rows[8][kWarpRowCap];
+    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
+    __shared__ ACC s_rows[8][kWarpRowCap];
 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -131,36 +236,11 @@ __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
     const int r1 = d.r1f & kChunkRowMask;
 
     if (d.r1f & kChunkLong) {
-        // one long row: lanes stride the row, then a butterfly reduction
-        ACC acc;
-        acc.zero();
-        for (int k = d.k0 + lane; k < d.k1; k += 32) {
-            const XT xv = __ldg(x + __ldg(m.col + k));
-            if constexpr (INDIRECT)
-                acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
-            else
-                acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
-        if (lane == 0) store_row(y, r0, acc.get(), alpha, beta, plain, m.rmap);
+        long_row<VT, XT, YT, ACC, INDIRECT>(m, d, x, y, alpha, beta, plain, lane);
         return;
     }
     if (d.r1f & kChunkEmpty) {
-        // chunk with empty rows: one row per lane
-        for (int r = r0 + lane; r < r1; r += 32) {
-            ACC acc;
-            acc.zero();
-            const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
-            for (int k = kb; k < ke; ++k) {
-                const XT xv = __ldg(x + __ldg(m.col + k));
-                if constexpr (INDIRECT)
-                    acc.fma(__ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k)), xv);
-                else
-                    acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
-            }
-            store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
-        }
+        rows_per_lane<VT, XT, YT, ACC, INDIRECT>(m, r0, r1, x, y, alpha, beta, plain, lane);
         return;
     }
 
@@ -177,7 +257,6 @@ __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
         const uint32_t word = __ldg(p.masks + w * MW + (lane >> 2));
         mbits = (word >> ((lane & 3) * 8)) & 0xffu;
     }
-
     VS vv[E];
     int32_t cc[E];
     XT xv[E];
@@ -191,85 +270,20 @@ __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
     VT vals[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        if constexpr (INDIRECT) {
-            vals[e] = VT(0);
-            if (e >= lo && e < hi) vals[e] = __ldg(static_cast<const VT *>(m.vind) + vv[e]);
-        } else {
-            vals[e] = vv[e];
-        }
-    }
-
-    // rows: exclusive prefix over lanes of the row starts in their slots
-    const int cnt = __popc(mbits);
-    int pre = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += t;
-    }
-    pre -= cnt;
-    const bool active = lo < hi;
-    const bool starts_first = active && ((mbits >> lo) & 1u);
-    int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
-    const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
-
-    double *srow = s_rows[wib];
-    ACC acc;
-    acc.zero();
-    ACC pend;
-    pend.zero();
-    bool started = starts_first;
-    bool has_pend = false;
-    int pend_row = row;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
+        vals[e] = VT(0);
         if (e >= lo && e < hi) {
-            if ((flush >> e) & 1u) {
-                if (started) srow[row - r0] = acc.get();
-                else { has_pend = true; pend = acc; }
-                ++row;
-                acc.zero();
-                started = true;
-            }
-            acc.fma(vals[e], xv[e]);
+            if constexpr (INDIRECT) vals[e] = __ldg(static_cast<const VT *>(m.vind) + vv[e]);
+            else vals[e] = vv[e];
         }
     }
-    // does the lane's last row end with its slots?
     const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
     const bool ends = (seg + E >= d.k1) || (lane < 31 && (next_bits & 1u));
-    bool carry = false;
-    if (active) {
-        if (ends) {
-            if (started) srow[row - r0] = acc.get();
-            else { has_pend = true; pend = acc; pend_row = row; }
-        } else {
-            carry = true;
-        }
-    }
-    // rows cut by lane boundaries: add the carries of the lanes before, in order
-    const bool through = carry && !started;  // the lane's slots lie inside one row
-    ACC tot = pend;
-    int dist = 1;
-    bool need = has_pend;
-    while (__any_sync(0xffffffffu, need)) {
-        const ACC c = shfl_up_acc(acc, dist);
-        const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
-        if (need) {
-            ACC t2 = c;
-            t2.add(tot);
-            tot = t2;
-            need = cthrough;
-        }
-        ++dist;
-    }
-    if (has_pend) srow[pend_row - r0] = tot.get();
+    ACC *srow = s_rows[wib];
+    chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
     __syncwarp();
-    for (int i = lane; i < r1 - r0; i += 32) store_row(y, r0 + i, srow[i], alpha, beta, plain, m.rmap);
+    for (int i = lane; i < r1 - r0; i += 32) store_row(y, r0 + i, srow[i].get(), alpha, beta, plain, m.rmap);
 }
 
-}  // namespace spmv
-
-namespace spmv {
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
 struct WarpKernel {
     static cudaError_t launch(const WarpParams &p, int n_chunks, cudaStream_t s) {
