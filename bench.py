@@ -45,7 +45,7 @@ TRAFFIC = {"kernel_hash": None, "bytes_per_launch": None}
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("warp_kernel.cuh", "common.cuh", "internal.h", "k_warp.cu"):
+    for f in ("pipe_kernel.cuh", "warp_kernel.cuh", "common.cuh", "internal.h", "k_warp_f64.cu"):
         with open(os.path.join(ROOT, "paper_1106_5908_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -327,7 +327,7 @@ def run_ours(args, rank, world, local_rank):
         "gflops": flops_step * K * world / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_warp<E=16,f64> plain FP64 product (warp-chunk kernel)",
+                     "kernel": "k_pipe<E,f64> plain FP64 product (pipelined warp-chunk kernel)",
                      "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "frac_of_8tbs_spec": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": b_plain},

@@ -27,6 +27,15 @@ bool tile_ops(int vk, int xk, int yk, int acc, int R, int E, bool indirect, bool
     }
     return tile_ops_f32(xk, yk, acc, R, E, indirect, batched, ops);
 }
+
+bool warp_ops(int vk, int xk, int yk, int acc, int E, bool indirect, bool batched, WarpOps *ops) {
+    if (vk == kF64) {
+        if (xk != kF64 || yk != kF64) return false;
+        return warp_ops_f64(E, indirect, batched, ops);
+    }
+    if (xk != kF32) return false;
+    return warp_ops_f32(yk, acc, E, indirect, batched, ops);
+}
 }  // namespace spmv
 
 using namespace spmv;
@@ -276,18 +285,21 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 }
 
 // Autotuner: from the row-length histogram choose the kernel and its work per
-// lane.  The warp-chunk kernel (family 0) keeps every FP64 FMA lane busy whatever
-// the row lengths, so it is the default; its entries per lane E is 16 (chunks of
-// 512 entries) unless rows are so short that the row cap of a chunk would leave
-// slots idle, then 8.  The row-vector kernel's lanes per row T (family 1) is the
-// power of two nearest half the mean row length, used when chosen explicitly.
+// lane.  The pipelined warp-chunk kernel (family 0, odd E) keeps every FP64 FMA
+// lane busy whatever the row lengths, so it is the default.  Its entries per lane
+// E is 7 (chunks of 224 entries, 32 warps per SM) for mean row lengths below 20
+// and 15 (chunks of 480 entries, 16 warps per SM) above: short rows gain from
+// the extra warps in flight, long rows from fewer rows cut by lane boundaries
+// (measured on the 7-point, Hamiltonian-like and 27-point matrices).  The
+// row-vector kernel's lanes per row T (family 1) is the power of two nearest
+// half the mean row length, used when chosen explicitly.
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
     h->family = 0;
-    h->E = (mean * kWarpRowCap >= 512.0) ? 16 : 8;
+    h->E = (mean < 20.0) ? 7 : 15;
 }
 
 ChunkTable *get_chunks(spmv_matrix *h, int E, bool transposed) {
@@ -958,8 +970,11 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         // through the permutation
         WarpOps ops;
         const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
-        if (!warp_ops(h->vk, h->vk, h->vk, acc, 16, true, false, &ops)) return SPMV_ERR_UNSUPPORTED;
-        ChunkTable *ct = get_chunks(h, 16, true);
+        const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
+        int ET = (meanT < 20.0) ? 7 : 15;
+        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, true, false, &ops)) ET = 15;
+        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, true, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+        ChunkTable *ct = get_chunks(h, ET, true);
         if (!ct) return SPMV_ERR_ALLOC;
         WarpParams wp{};
         wp.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr};
@@ -1024,8 +1039,8 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
         nnz += mats[m]->nnz;
         rows += mats[m]->n_rows;
     }
-    b->E = (rows && static_cast<double>(nnz) / rows * kWarpRowCap < 512.0) ? 8 : 16;
-    if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) b->E = 16;
+    b->E = (rows && static_cast<double>(nnz) / rows < 20.0) ? 7 : 15;
+    if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) b->E = 15;
     if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) {
         delete b;
         return SPMV_ERR_UNSUPPORTED;

@@ -81,6 +81,8 @@ struct WarpOps {
     cudaError_t (*launch)(const WarpParams &, int n_chunks, cudaStream_t);
 };
 bool warp_ops(int vk, int xk, int yk, int acc, int E, bool indirect, bool batched, WarpOps *ops);
+bool warp_ops_f64(int E, bool indirect, bool batched, WarpOps *ops);
+bool warp_ops_f32(int yk, int acc, int E, bool indirect, bool batched, WarpOps *ops);
 
 cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
                           int T, cudaStream_t s);
