@@ -191,6 +191,37 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
 spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_idx,
                                int32_t *perm, void *stream);
 
+/* Transposed CRS build that allocates nothing (no counterpart in the paper).
+ *
+ * Some callers cannot allocate device memory at the moment they need this
+ * result: code running while a CUDA graph is being captured (cudaMalloc is not
+ * a capturable operation), real-time or latency-bound loops that must not wait
+ * on the allocator or risk an out-of-memory failure mid-run, and programs whose
+ * device memory is already reserved by another allocator.  This entry point
+ * builds the same structure as spmv_get_transpose from CRS arrays already on
+ * the device and writes it to caller-provided device buffers; its scratch (one
+ * counter per column plus the scan's block sums) is a fixed array compiled into
+ * the library, which every GPU that loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   row_ptr[n_rows+1], col_idx[nnz]: a valid CRS structure on the device;
+ *   rowT_ptr[n_cols+1], colT_idx[nnz], perm[nnz]: device outputs, as for
+ *   spmv_get_transpose (rows of A^T in increasing position of A).
+ * n_cols must not exceed SPMV_NOALLOC_MAX_COLS (larger sizes return
+ * SPMV_ERR_UNSUPPORTED before any work is enqueued).  Entries outside the CRS
+ * rules are skipped rather than followed, so the output is then not a
+ * transpose, but no memory outside the arrays is touched.
+ * The first call on a device looks up the scratch array's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call shares the one array and re-clears the part it
+ * uses, so calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be ordered by the caller.  Asynchronous on stream. */
+#define SPMV_NOALLOC_MAX_COLS (1 << 20)
+spmv_status spmv_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                   const int32_t *row_ptr, const int32_t *col_idx,
+                                   int32_t *rowT_ptr, int32_t *colT_idx, int32_t *perm,
+                                   void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched persistent launch                                                   */
 /* ------------------------------------------------------------------------ */

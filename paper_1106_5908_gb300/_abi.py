@@ -24,13 +24,14 @@ SPMV_ERR_NOT_CONVERGED = 7
 
 SPMV_F64 = 0
 SPMV_F32 = 1
+SPMV_NOALLOC_MAX_COLS = 1 << 20
 
 # Every entry point declared in include/spmv.h.
 EXPORTS = (
     "spmv_status_string", "spmv_version", "spmv_create", "spmv_destroy", "spmv_set_values",
     "spmv_get_info", "spmv_row_histogram", "spmv_set_plan", "spmv_set_accumulator", "spmv_apply", "spmv_split_create",
     "spmv_split_destroy", "spmv_split_get_plan", "spmv_apply_split", "spmv_split_get_halo",
-    "spmm_apply", "spmv_backward", "spmv_get_transpose", "spmv_batched_create",
+    "spmm_apply", "spmv_backward", "spmv_get_transpose", "spmv_transpose_noalloc", "spmv_batched_create",
     "spmv_batched_destroy", "spmv_batched_apply", "spmv_batched_get_info", "spmv_ir_cg",
     "spmv_cg", "spmv_check_device_error",
 )
@@ -80,6 +81,7 @@ def load() -> ctypes.CDLL:
         "spmm_apply": (st, [vp, i32, f64, vp, f64, vp, st, vp]),
         "spmv_backward": (st, [vp, f64, vp, vp, vp, vp, vp]),
         "spmv_get_transpose": (st, [vp, vp, vp, vp, vp]),
+        "spmv_transpose_noalloc": (st, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
         "spmv_batched_create": (st, [vp, i32, vp]),
         "spmv_batched_destroy": (None, [vp]),
         "spmv_batched_apply": (st, [vp, f64, vp, f64, vp, vp]),
@@ -133,6 +135,7 @@ spmv_split_get_halo = _fwd("spmv_split_get_halo")
 spmm_apply = _fwd("spmm_apply")
 spmv_backward = _fwd("spmv_backward")
 spmv_get_transpose = _fwd("spmv_get_transpose")
+spmv_transpose_noalloc = _fwd("spmv_transpose_noalloc")
 spmv_batched_create = _fwd("spmv_batched_create")
 spmv_batched_destroy = _fwd("spmv_batched_destroy")
 spmv_batched_apply = _fwd("spmv_batched_apply")

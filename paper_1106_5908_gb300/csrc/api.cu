@@ -1013,6 +1013,18 @@ spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_i
     return SPMV_OK;
 }
 
+spmv_status spmv_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                   const int32_t *row_ptr, const int32_t *col_idx,
+                                   int32_t *rowT_ptr, int32_t *colT_idx, int32_t *perm,
+                                   void *stream) {
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return SPMV_ERR_INVALID_ARG;
+    if (n_cols > transpose_noalloc_max_cols()) return SPMV_ERR_UNSUPPORTED;
+    if (!row_ptr || !rowT_ptr || (nnz > 0 && (!col_idx || !colT_idx || !perm))) return SPMV_ERR_INVALID_ARG;
+    cudaError_t e = launch_transpose_noalloc(n_rows, n_cols, nnz, row_ptr, col_idx, rowT_ptr, colT_idx,
+                                             perm, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // Batched persistent launch
 // ---------------------------------------------------------------------------

@@ -101,6 +101,13 @@ cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const 
                              const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
                              int32_t *work, cudaStream_t s);
 
+// Transposed structure into caller buffers with the fixed device work array
+// (no allocation); n_cols <= transpose_noalloc_max_cols().
+cudaError_t launch_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                     const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
+                                     cudaStream_t s);
+int64_t transpose_noalloc_max_cols();
+
 // Value conversion (FP64 <-> FP32), n entries.
 cudaError_t launch_convert(const void *src, int sk, void *dst, int dk, int64_t n, cudaStream_t s);
 

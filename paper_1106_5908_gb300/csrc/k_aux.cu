@@ -358,6 +358,103 @@ int64_t transpose_work_len(int32_t n_cols) {
 }
 
 // ---------------------------------------------------------------------------
+// Transposed build without allocation.  Its work array (column counts, then
+// cursors, then the scan's block sums) lives in one fixed device array that
+// every GPU loading the library holds until the process exits.  Entries whose
+// column or row range is outside the stated sizes are skipped, so a malformed
+// input cannot make these kernels touch memory outside their arrays.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxCols = 1 << 20;
+constexpr int64_t kNoAllocWorkLen = kNoAllocMaxCols + 1 + (kNoAllocMaxCols + kScanChunk - 1) / kScanChunk + 1;
+static __device__ __align__(256) int32_t g_transpose_scratch[kNoAllocWorkLen];
+
+__global__ void k_count_cols_checked(const int32_t *__restrict__ col, int64_t nnz, int32_t n_cols,
+                                     int32_t *cnt) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nnz;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t c = __ldg(col + k);
+        if (c >= 0 && c < n_cols) atomicAdd(cnt + c, 1);
+    }
+}
+
+__global__ void k_fill_transpose_checked(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                         int32_t n_rows, int32_t n_cols, int64_t nnz, int32_t *cursor,
+                                         int32_t *colT, int32_t *perm) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_rows;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t kb = max(static_cast<int64_t>(rp[i]), static_cast<int64_t>(0));
+        const int64_t ke = min(static_cast<int64_t>(rp[i + 1]), nnz);
+        for (int64_t k = kb; k < ke; ++k) {
+            const int32_t c = col[k];
+            if (c < 0 || c >= n_cols) continue;
+            const int pos = atomicAdd(cursor + c, 1);
+            if (pos >= 0 && pos < nnz) {
+                colT[pos] = static_cast<int32_t>(i);
+                perm[pos] = static_cast<int32_t>(k);
+            }
+        }
+    }
+}
+
+int64_t transpose_noalloc_max_cols() { return kNoAllocMaxCols; }
+
+// Device address of the fixed work array on the current device, looked up once
+// per device (host code cannot use the array's name as a device address).
+static int32_t *noalloc_scratch_ptr(cudaError_t *err) {
+    constexpr int kMaxDevices = 64;
+    static int32_t *ptrs[kMaxDevices] = {nullptr};
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (ptrs[dev] == nullptr) {
+        void *p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_transpose_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int32_t *>(p);
+    }
+    *err = cudaSuccess;
+    return ptrs[dev];
+}
+
+cudaError_t launch_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                     const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
+                                     cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    int32_t *work = noalloc_scratch_ptr(&e);
+    if (!work) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the array keeps the previous call's contents: clear the counts first
+    e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (static_cast<size_t>(n_cols) + 1), s);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) k_count_cols_checked<<<8 * sms, 256, 0, s>>>(col, nnz, n_cols, work);
+    const int64_t nb = (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk;
+    int32_t *sums = work + n_cols + 1;
+    if (n_cols > 0) {
+        k_scan_partial<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums);
+        k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, static_cast<int32_t>(nb));
+        k_scan_final<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums, rowT);
+    } else {
+        e = cudaMemsetAsync(rowT, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (nnz > 0) {
+        e = cudaMemcpyAsync(work, rowT, sizeof(int32_t) * static_cast<size_t>(n_cols),
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        k_fill_transpose_checked<<<4 * sms, 256, 0, s>>>(rp, col, n_rows, n_cols, nnz, work, colT, perm);
+        k_sort_rowsT<<<4 * sms, 256, 0, s>>>(rowT, n_cols, colT, perm);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Conversions and fills.
 // ---------------------------------------------------------------------------
 __global__ void k_f64_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
