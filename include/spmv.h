@@ -101,10 +101,13 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
  * counts is a HOST array of nbins int64. */
 spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
 
-/* Override the autotuner's choice of kernel family and per-thread work.
- * family: 0 = nnz-split tile kernel, 1 = row-vector kernel; param = E (odd,
- * 3..31) for family 0, threads per row (1,2,4,8,16,32) for family 1; 0 keeps the
- * tuned value.  Results are unchanged up to summation order. */
+/* Override the autotuner's choice of kernel family and work per lane/thread.
+ * family 0: warp-chunk kernel, param = entries per lane E (7 or 15: pipelined
+ *           through a two-stage shared-memory ring; 8 or 16: direct loads);
+ * family 1: row-vector kernel, param = threads per row (1,2,4,8,16,32);
+ * family 2: staged tile kernel, param = entries per thread segment (odd, 3..31);
+ * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7 or 15.
+ * param 0 keeps a default.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
 /* Accumulator of an FP32-storage handle: 0 = one FP64 FMA per entry (operands

@@ -447,10 +447,12 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
                        int yk, cudaStream_t s) {
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-    if (h->family == 0 || h->d_rmap) {
+    if (h->family == 0 || h->family == 3 || h->d_rmap) {
         int E = h->E;
         WarpOps ops;
-        if (!warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) {
+        // family 3 selects the three-stage kernel of the same chunking
+        const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
+        if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) {
             E = 16;
             if (!warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) return SPMV_ERR_UNSUPPORTED;
         }
@@ -682,7 +684,13 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 }
 
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
-    if (!h || family < 0 || family > 2) return SPMV_ERR_INVALID_ARG;
+    if (!h || family < 0 || family > 3) return SPMV_ERR_INVALID_ARG;
+    if (family == 3) {
+        if (param != 0 && param != 7 && param != 15) return SPMV_ERR_INVALID_ARG;
+        h->family = 3;
+        h->E = param ? param : 7;
+        return SPMV_OK;
+    }
     if (family == 0) {
         if (param != 0 && param != 7 && param != 8 && param != 15 && param != 16) return SPMV_ERR_INVALID_ARG;
         h->family = 0;

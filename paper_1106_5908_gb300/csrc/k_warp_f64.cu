@@ -13,6 +13,14 @@ bool warp_ops_f64(int E, bool indirect, bool batched, WarpOps *ops) {
         ops->launch = &PipeKernel<E_, double, double, double, AccF64, IND_, BAT_>::launch; \
         return true;                                                                       \
     }
+#define SPMV_P3(E_, BAT_)                                                                   \
+    if (E == E_ + 100 && !indirect && batched == BAT_) {                                   \
+        ops->launch = &Pipe3Kernel<E_, double, double, double, AccF64, false, BAT_>::launch; \
+        return true;                                                                       \
+    }
+    SPMV_P3(7, false)
+    SPMV_P3(15, false)
+#undef SPMV_P3
 #define SPMV_W(E_, IND_, BAT_)                                                             \
     if (E == E_ && indirect == IND_ && batched == BAT_) {                                  \
         ops->launch = &WarpKernel<E_, double, double, double, AccF64, IND_, BAT_>::launch; \

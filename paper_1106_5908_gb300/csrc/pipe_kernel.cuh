@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
     static_assert(E % 2 == 1, "odd E: conflict-free strided shared-memory reads");
     using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
     using L = PipeLayout<E, VS>;
-    constexpr int SLOTS = L::SLOTS;
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int lane = threadIdx.x & 31;
@@ -170,6 +169,211 @@ struct PipeKernel {
     using VS = typename std::conditional<INDIRECT, int32_t, VT>::type;
     using L = PipeLayout<E, VS>;
     static constexpr auto fn = k_pipe<E, VT, XT, YT, ACC, INDIRECT, BATCHED>;
+    static int grid_limit() {
+        static int cached = -1;
+        static int cached_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cached >= 0 && cached_dev == dev) return cached;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(L::block_bytes)) != cudaSuccess)
+            return 0;
+        int per_sm = 0, sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, L::block_bytes) != cudaSuccess)
+            return 0;
+        cached = per_sm * sms;
+        cached_dev = dev;
+        return cached;
+    }
+    static cudaError_t launch(const WarpParams &p, int n_chunks, cudaStream_t s) {
+        if (n_chunks <= 0) return cudaSuccess;
+        const int lim = grid_limit();
+        if (lim <= 0) return cudaErrorInvalidConfiguration;
+        const int want = (n_chunks + 7) / 8;
+        fn<<<want < lim ? want : lim, 256, L::block_bytes, s>>>(p);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace spmv
+
+namespace spmv {
+
+// Three-stage variant: the x gathers of chunk i+1 are issued before the FMA
+// chains of chunk i, so one warp keeps its next chunk's L2 gathers in flight
+// while its FP64 chain runs; chunk i+2 is being copied meanwhile.
+template <int E, typename VS>
+struct Pipe3Layout {
+    static constexpr int SLOTS = 32 * E;
+    static constexpr int SL = SLOTS + 4;
+    static constexpr int MWP = ((E + 3) / 4) * 4;
+    static constexpr size_t al(size_t v) { return (v + 15) & ~size_t(15); }
+    static constexpr size_t off_vs = 0;
+    static constexpr size_t off_col = off_vs + al(sizeof(VS) * SL);
+    static constexpr size_t off_mask = off_col + al(4 * SL);
+    static constexpr size_t off_desc = off_mask + al(4 * MWP);
+    static constexpr size_t stage = off_desc + 16;
+    static constexpr size_t off_rows = 3 * stage;
+    static constexpr size_t off_bar = off_rows + 8 * kWarpRowCap;
+    static constexpr size_t warp_bytes = al(off_bar + 24);
+    static constexpr size_t block_bytes = 8 * warp_bytes;
+};
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+__global__ void __launch_bounds__(256, (E <= 7) ? 3 : 1) k_pipe3(const WarpParams p) {
+    static_assert(E % 2 == 1, "odd E: conflict-free strided shared-memory reads");
+    static_assert(!INDIRECT, "values read from the staged copy");
+    using VS = VT;
+    using L = Pipe3Layout<E, VS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char *ws = smem + wib * L::warp_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L::off_bar);
+    ACC *srow = reinterpret_cast<ACC *>(ws + L::off_rows);
+    const int nwarps = gridDim.x * 8;
+    const int c0 = blockIdx.x * 8 + wib;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (c0 >= p.n_chunks) return;
+
+    uint64_t policy = 0;
+    if (lane == 0) policy = l2_evict_first_policy();
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+    auto is_regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
+    auto mat_of = [&](int cc) -> MatRef {
+        if constexpr (BATCHED) return p.mats[p.cmat[cc]];
+        else return p.m;
+    };
+    auto issue = [&](int cc, const ChunkDesc &d, int s) {
+        unsigned char *st = ws + s * L::stage;
+        *reinterpret_cast<ChunkDesc *>(st + L::off_desc) = d;
+        if (is_regular(d)) {
+            const MatRef m = mat_of(cc);
+            const int base = d.k0 & ~3;
+            const int n = ((d.k1 - base) + 3) & ~3;
+            const uint32_t bv = static_cast<uint32_t>(n * sizeof(VS));
+            const uint32_t bc = static_cast<uint32_t>(n * 4);
+            const uint32_t bm = static_cast<uint32_t>(L::MWP * 4);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[s], bv + bc + bm);
+            bulk_g2s(st + L::off_vs, static_cast<const VS *>(m.vs) + base, bv, &bar[s], policy);
+            bulk_g2s(st + L::off_col, m.col + base, bc, &bar[s], policy);
+            bulk_g2s(st + L::off_mask, p.masks + static_cast<int64_t>(cc) * L::MWP, bm, &bar[s], policy);
+        } else {
+            mbar_arrive(&bar[s]);
+        }
+    };
+    uint32_t phase = 0;  // bit s: parity of the next completion of stage s
+    auto wait_stage = [&](int s) -> bool {
+        bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+        phase ^= 1u << s;
+        return __all_sync(0xffffffffu, ok);
+    };
+    // gathers of the chunk staged in s (regular chunks only)
+    auto gather = [&](int cc, int s, XT (&xv)[E]) {
+        const unsigned char *st = ws + s * L::stage;
+        const ChunkDesc d = *reinterpret_cast<const ChunkDesc *>(st + L::off_desc);
+#pragma unroll
+        for (int e = 0; e < E; ++e) xv[e] = XT(0);
+        if (!is_regular(d)) return;
+        const MatRef m = mat_of(cc);
+        const XT *__restrict__ x = static_cast<const XT *>(m.x);
+        const int32_t *sc = reinterpret_cast<const int32_t *>(st + L::off_col);
+        const int base = d.k0 & ~3;
+        const int off = lane * E;
+        const int lo = max(0, d.k0 - base - off);
+        const int hi = min(E, d.k1 - base - off);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (e >= lo && e < hi) xv[e] = __ldg(x + sc[off + e]);
+    };
+
+    // prologue: chunks c0 and c0+nwarps in flight, gathers of c0 issued
+    ChunkDesc dnext{};
+    if (lane == 0) {
+        issue(c0, p.chunks[c0], 0);
+        if (c0 + nwarps < p.n_chunks) {
+            issue(c0 + nwarps, p.chunks[c0 + nwarps], 1);
+            if (c0 + 2 * nwarps < p.n_chunks) dnext = p.chunks[c0 + 2 * nwarps];
+        }
+    }
+    XT xcur[E];
+    if (!wait_stage(0)) {
+        if (lane == 0) set_error(p.err, kDevErrTimeout);
+        return;
+    }
+    gather(c0, 0, xcur);
+
+    int s = 0;
+    for (int c = c0; c < p.n_chunks; c += nwarps) {
+        const int c1 = c + nwarps, c2 = c + 2 * nwarps;
+        const int s1 = (s + 1) % 3, s2 = (s + 2) % 3;
+        if (lane == 0 && c2 < p.n_chunks) {
+            issue(c2, dnext, s2);
+            if (c2 + nwarps < p.n_chunks) dnext = p.chunks[c2 + nwarps];
+        }
+        XT xnext[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) xnext[e] = XT(0);
+        if (c1 < p.n_chunks) {
+            if (!wait_stage(s1)) {
+                if (lane == 0) set_error(p.err, kDevErrTimeout);
+                return;
+            }
+            gather(c1, s1, xnext);
+        }
+        // ---- chunk c (staged in s, gathers in xcur) --------------------------
+        const unsigned char *st = ws + s * L::stage;
+        const ChunkDesc d = *reinterpret_cast<const ChunkDesc *>(st + L::off_desc);
+        const MatRef m = mat_of(c);
+        const XT *__restrict__ x = static_cast<const XT *>(m.x);
+        YT *__restrict__ y = static_cast<YT *>(m.y);
+        const int r0 = d.r0;
+        const int r1 = d.r1f & kChunkRowMask;
+        if (d.r1f & kChunkLong) {
+            long_row<VT, XT, YT, ACC, false>(m, d, x, y, alpha, beta, plain, lane);
+        } else if (d.r1f & kChunkEmpty) {
+            rows_per_lane<VT, XT, YT, ACC, false>(m, r0, r1, x, y, alpha, beta, plain, lane);
+        } else {
+            const VS *sv = reinterpret_cast<const VS *>(st + L::off_vs);
+            const uint32_t *smk = reinterpret_cast<const uint32_t *>(st + L::off_mask);
+            const int base = d.k0 & ~3;
+            const int off = lane * E;
+            const int lo = max(0, d.k0 - base - off);
+            const int hi = min(E, d.k1 - base - off);
+            const int w0 = off >> 5, sh = off & 31;
+            const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
+            const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
+            VT vals[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) vals[e] = (e >= lo && e < hi) ? sv[off + e] : VT(0);
+            const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
+            const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
+            chunk_lane<E, VT, XT, ACC>(vals, xcur, mbits, lo, hi, ends, r0, srow, lane);
+            __syncwarp();
+            for (int q = lane; q < r1 - r0; q += 32)
+                store_row(y, r0 + q, srow[q].get(), alpha, beta, plain, m.rmap);
+        }
+        __syncwarp();  // stage s and the row buffer are free again
+#pragma unroll
+        for (int e = 0; e < E; ++e) xcur[e] = xnext[e];
+        s = s1;
+    }
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
+struct Pipe3Kernel {
+    using L = Pipe3Layout<E, VT>;
+    static constexpr auto fn = k_pipe3<E, VT, XT, YT, ACC, INDIRECT, BATCHED>;
     static int grid_limit() {
         static int cached = -1;
         static int cached_dev = -1;

@@ -35,7 +35,7 @@ struct alignas(16) ChunkDesc {
 constexpr int32_t kChunkLong = 1 << 30;   // one row longer than a chunk
 constexpr int32_t kChunkEmpty = 1 << 29;  // chunk contains empty rows
 constexpr int32_t kChunkRowMask = (1 << 29) - 1;
-constexpr int kWarpRowCap = 128;          // rows per chunk (per-warp row buffer)
+constexpr int kWarpRowCap = 96;           // rows per chunk (per-warp row buffer)
 
 struct WarpParams {
     MatRef m;

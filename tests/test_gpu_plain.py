@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 15), (0, 7), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
 
 
 def make(A, dtype=None):
@@ -40,7 +40,7 @@ def test_random_plans(shape, plan):
         assert_within(host(y), ref, bound, 1e-13, f"plan {plan} a={alpha} b={beta}")
 
 
-@pytest.mark.parametrize("plan", PLANS[:7])
+@pytest.mark.parametrize("plan", PLANS[:9])
 @pytest.mark.parametrize("long_len", [253, 257, 509, 513, 1791, 1793, 3841, 9000, 40000])
 def test_long_rows(plan, long_len):
     """Rows longer than a tile take the CTA-wide path; mixed with short ones."""
