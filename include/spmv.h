@@ -106,7 +106,7 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  *           through a two-stage shared-memory ring; 8 or 16: direct loads);
  * family 1: row-vector kernel, param = threads per row (1,2,4,8,16,32);
  * family 2: staged tile kernel, param = entries per thread segment (odd, 3..31);
- * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7 or 15.
+ * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7, 11, 15.
  * param 0 keeps a default.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 

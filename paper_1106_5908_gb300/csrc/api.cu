@@ -3,6 +3,7 @@
 // pass, the batched graph launch and the CG solvers.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -193,7 +194,8 @@ struct spmv_matrix {
     int32_t *d_err = nullptr;
     std::vector<int32_t> h_rp;
     // plan
-    int family = 0;  // 0 warp chunks, 1 row-vector, 2 staged tiles
+    double col_random = 0.0;  // column_randomness() of the pattern
+    int family = 0;  // 0 warp chunks, 1 row-vector, 2 staged tiles, 3 three-stage chunks
     int E = 16;      // entries per lane (family 0) or per thread segment (family 2)
     int T = 8;
     int acc32 = kAccFF;
@@ -298,8 +300,39 @@ void autotune(spmv_matrix *h) {
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
-    h->family = 0;
-    h->E = (mean < 20.0) ? 7 : 15;
+    if (h->col_random > 0.25) {
+        // many columns far from those of the row before: the x gathers miss L1,
+        // so gather one chunk ahead (three-stage kernel)
+        h->family = 3;
+        h->E = 15;
+    } else {
+        h->family = 0;
+        h->E = (mean < 20.0) ? 7 : 15;
+    }
+}
+
+// Share of entries (sampled rows) whose column is more than 8 away from every
+// column of the previous row: near 0 for stencils and banded matrices, large for
+// scattered patterns whose x gathers find nothing in L1.
+double column_randomness(const int32_t *rp, const int32_t *col, int32_t n_rows) {
+    if (!col || n_rows < 2) return 0.0;
+    const int32_t step = std::max<int32_t>(1, n_rows / 32768);
+    int64_t far = 0, total = 0;
+    std::vector<int32_t> prev;
+    for (int32_t i = 1; i < n_rows; i += step) {
+        prev.assign(col + rp[i - 1], col + rp[i]);
+        std::sort(prev.begin(), prev.end());
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int32_t c = col[k];
+            auto it = std::lower_bound(prev.begin(), prev.end(), c);
+            int64_t best = INT64_MAX;
+            if (it != prev.end()) best = static_cast<int64_t>(*it) - c;
+            if (it != prev.begin()) best = std::min<int64_t>(best, static_cast<int64_t>(c) - *(it - 1));
+            far += (best > 8) ? 1 : 0;
+            ++total;
+        }
+    }
+    return total ? static_cast<double>(far) / total : 0.0;
 }
 
 ChunkTable *get_chunks(spmv_matrix *h, int E, bool transposed) {
@@ -394,7 +427,8 @@ void destroy_matrix(spmv_matrix *h) {
 
 spmv_status create_from_host(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_t nnz,
                              std::vector<int32_t> &&h_rp, const int32_t *col_idx, const void *val,
-                             int val_t, int store_t, bool dev_ptrs, cudaStream_t s) {
+                             int val_t, int store_t, bool dev_ptrs, cudaStream_t s,
+                             const int32_t *host_col) {
     spmv_matrix *h = new (std::nothrow) spmv_matrix();
     if (!h) return SPMV_ERR_ALLOC;
     cudaGetDevice(&h->device);
@@ -403,6 +437,7 @@ spmv_status create_from_host(spmv_handle *out, int32_t n_rows, int32_t n_cols, i
     h->nnz = nnz;
     h->vk = store_t;
     h->h_rp = std::move(h_rp);
+    h->col_random = column_randomness(h->h_rp.data(), host_col, n_rows);
     spmv_status st = upload_matrix(h, nullptr, col_idx, val, val_t, dev_ptrs, s);
     if (st != SPMV_OK) {
         destroy_matrix(h);
@@ -551,6 +586,7 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
     m->d_rp = h->d_rp;
     m->d_col = h->d_col;
     m->h_rp = h->h_rp;
+    m->col_random = h->col_random;
     const size_t nent = static_cast<size_t>(h->nnz) + kEntryPad;
     if (cudaMalloc(&m->d_val, nent * 4) != cudaSuccess || dmalloc(&m->d_err, 1) != cudaSuccess) {
         destroy_matrix(m);
@@ -613,7 +649,7 @@ spmv_status spmv_create(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_
     spmv_status st = validate_host(n_rows, n_cols, nnz, h_rp.data(), col_host);
     if (st != SPMV_OK) return st;
     return create_from_host(out, n_rows, n_cols, nnz, std::move(h_rp), col_idx, val, val_t, val_t,
-                            is_device_ptr != 0, s);
+                            is_device_ptr != 0, s, col_host);
 }
 
 void spmv_destroy(spmv_handle h) { destroy_matrix(h); }
@@ -653,7 +689,8 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
             }
         } else {
             WarpOps ops;
-            if (!warp_ops(h->vk, h->vk, h->vk, acc, E, false, false, &ops)) E = 16;
+            const bool ok3 = h->family == 3 && warp_ops(h->vk, h->vk, h->vk, acc, E + 100, false, false, &ops);
+            if (!ok3 && !warp_ops(h->vk, h->vk, h->vk, acc, E, false, false, &ops)) E = 16;
             ChunkTable *ct = get_chunks(h, E, false);
             if (ct) {
                 nunits = ct->n;
@@ -686,7 +723,7 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
     if (!h || family < 0 || family > 3) return SPMV_ERR_INVALID_ARG;
     if (family == 3) {
-        if (param != 0 && param != 7 && param != 15) return SPMV_ERR_INVALID_ARG;
+        if (param != 0 && param != 7 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
         h->family = 3;
         h->E = param ? param : 7;
         return SPMV_OK;
@@ -820,7 +857,7 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
     cudaStream_t s = nullptr;
     spmv_status st = create_from_host(&sp->Aloc, n, n, static_cast<int64_t>(col_loc.size()),
                                       std::vector<int32_t>(rp_loc), col_loc.data(), val_loc.data(),
-                                      kF64, kF64, false, s);
+                                      kF64, kF64, false, s, col_loc.data());
     // the nonlocal part keeps only rows with nonlocal entries; each stored row
     // carries the output row it updates
     std::vector<int32_t> nl_rows, rp_c(1, 0);
@@ -832,7 +869,7 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
     if (st == SPMV_OK)
         st = create_from_host(&sp->Anl, static_cast<int32_t>(nl_rows.size()), static_cast<int32_t>(sp->total_halo),
                               static_cast<int64_t>(col_nl.size()), std::move(rp_c),
-                              col_nl.data(), val_nl.data(), kF64, kF64, false, s);
+                              col_nl.data(), val_nl.data(), kF64, kF64, false, s, nullptr);
     if (st == SPMV_OK) {
         if (dmalloc(&sp->Anl->d_rmap, nl_rows.size()) != cudaSuccess) st = SPMV_ERR_ALLOC;
         else if (!nl_rows.empty() && cudaMemcpy(sp->Anl->d_rmap, nl_rows.data(), 4 * nl_rows.size(),
@@ -856,8 +893,12 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
         return st;
     }
     // the split parts use the tile kernel with the parent's per-thread work
-    sp->Aloc->family = 0;
-    sp->Anl->family = 0;
+    // the split parts use the tuned chunk kernels; the nonlocal columns index the
+    // halo, not rows, so gather one chunk ahead there
+    if (sp->Anl->vk == kF64) {
+        sp->Anl->family = 3;
+        sp->Anl->E = 15;
+    }
     if (halo_count_out)
         for (int b = 0; b < nblocks; ++b) halo_count_out[b] = sp->halo_count[b];
     *out = sp;

@@ -11,6 +11,16 @@ bool warp_ops_f32(int yk, int acc, int E, bool indirect, bool batched, WarpOps *
         ops->launch = &PipeKernel<E_, float, float, YT_, ACC_, IND_, BAT_>::launch;     \
         return true;                                                                    \
     }
+#define SPMV_P3(YK_, YT_, ACCK_, ACC_, E_)                                                \
+    if (yk == YK_ && acc == ACCK_ && E == E_ + 100 && !indirect && !batched) {          \
+        ops->launch = &Pipe3Kernel<E_, float, float, YT_, ACC_, false, false>::launch;  \
+        return true;                                                                    \
+    }
+    SPMV_P3(kF32, float, kAccFF, AccFF, 15)
+    SPMV_P3(kF64, double, kAccFF, AccFF, 15)
+    SPMV_P3(kF32, float, kAccF64, AccF64, 15)
+    SPMV_P3(kF64, double, kAccF64, AccF64, 15)
+#undef SPMV_P3
 #define SPMV_W(YK_, YT_, ACCK_, ACC_, E_, IND_, BAT_)                                   \
     if (yk == YK_ && acc == ACCK_ && E == E_ && indirect == IND_ && batched == BAT_) {  \
         ops->launch = &WarpKernel<E_, float, float, YT_, ACC_, IND_, BAT_>::launch;     \

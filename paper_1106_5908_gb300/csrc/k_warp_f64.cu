@@ -19,6 +19,7 @@ bool warp_ops_f64(int E, bool indirect, bool batched, WarpOps *ops) {
         return true;                                                                       \
     }
     SPMV_P3(7, false)
+    SPMV_P3(11, false)
     SPMV_P3(15, false)
 #undef SPMV_P3
 #define SPMV_W(E_, IND_, BAT_)                                                             \

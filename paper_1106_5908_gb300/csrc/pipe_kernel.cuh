@@ -203,7 +203,7 @@ namespace spmv {
 // Three-stage variant: the x gathers of chunk i+1 are issued before the FMA
 // chains of chunk i, so one warp keeps its next chunk's L2 gathers in flight
 // while its FP64 chain runs; chunk i+2 is being copied meanwhile.
-template <int E, typename VS>
+template <int E, typename VS, int WPB>
 struct Pipe3Layout {
     static constexpr int SLOTS = 32 * E;
     static constexpr int SL = SLOTS + 4;
@@ -217,15 +217,24 @@ struct Pipe3Layout {
     static constexpr size_t off_rows = 3 * stage;
     static constexpr size_t off_bar = off_rows + 8 * kWarpRowCap;
     static constexpr size_t warp_bytes = al(off_bar + 24);
-    static constexpr size_t block_bytes = 8 * warp_bytes;
+    static constexpr size_t block_bytes = WPB * warp_bytes;
+    // resident blocks per SM that shared memory allows (227 KB usable)
+    static constexpr int min_blocks = (232448 / (block_bytes + 1024)) < 1 ? 1
+                                      : ((232448 / (block_bytes + 1024)) > 4 ? 4 : (232448 / (block_bytes + 1024)));
 };
 
+// warps per block of the three-stage kernel (fewer resident warps leave more of
+// the SM's 256 KB to L1, which holds the x lines near columns reuse)
+template <int E> struct Pipe3Warps { static constexpr int value = 8; };
+
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
-__global__ void __launch_bounds__(256, (E <= 7) ? 3 : 1) k_pipe3(const WarpParams p) {
+__global__ void __launch_bounds__(32 * Pipe3Warps<E>::value, Pipe3Layout<E, VT, Pipe3Warps<E>::value>::min_blocks)
+k_pipe3(const WarpParams p) {
     static_assert(E % 2 == 1, "odd E: conflict-free strided shared-memory reads");
     static_assert(!INDIRECT, "values read from the staged copy");
     using VS = VT;
-    using L = Pipe3Layout<E, VS>;
+    constexpr int WPB = Pipe3Warps<E>::value;
+    using L = Pipe3Layout<E, VS, WPB>;
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int lane = threadIdx.x & 31;
@@ -233,8 +242,8 @@ __global__ void __launch_bounds__(256, (E <= 7) ? 3 : 1) k_pipe3(const WarpParam
     unsigned char *ws = smem + wib * L::warp_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(ws + L::off_bar);
     ACC *srow = reinterpret_cast<ACC *>(ws + L::off_rows);
-    const int nwarps = gridDim.x * 8;
-    const int c0 = blockIdx.x * 8 + wib;
+    const int nwarps = gridDim.x * WPB;
+    const int c0 = blockIdx.x * WPB + wib;
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -372,7 +381,8 @@ __global__ void __launch_bounds__(256, (E <= 7) ? 3 : 1) k_pipe3(const WarpParam
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
 struct Pipe3Kernel {
-    using L = Pipe3Layout<E, VT>;
+    static constexpr int WPB = Pipe3Warps<E>::value;
+    using L = Pipe3Layout<E, VT, WPB>;
     static constexpr auto fn = k_pipe3<E, VT, XT, YT, ACC, INDIRECT, BATCHED>;
     static int grid_limit() {
         static int cached = -1;
@@ -385,7 +395,7 @@ struct Pipe3Kernel {
             return 0;
         int per_sm = 0, sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, L::block_bytes) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * WPB, L::block_bytes) != cudaSuccess)
             return 0;
         cached = per_sm * sms;
         cached_dev = dev;
@@ -395,8 +405,8 @@ struct Pipe3Kernel {
         if (n_chunks <= 0) return cudaSuccess;
         const int lim = grid_limit();
         if (lim <= 0) return cudaErrorInvalidConfiguration;
-        const int want = (n_chunks + 7) / 8;
-        fn<<<want < lim ? want : lim, 256, L::block_bytes, s>>>(p);
+        const int want = (n_chunks + WPB - 1) / WPB;
+        fn<<<want < lim ? want : lim, 32 * WPB, L::block_bytes, s>>>(p);
         return cudaGetLastError();
     }
 };

@@ -182,3 +182,18 @@ def test_laplace3d_160_fp32(c3):
     x = W.uniform(A.n_rows, W.SEED_C3_B).astype(np.float32)
     ref, bound = oracle.spmv(*A.astuple(), x.astype(np.float64), with_bound=True)
     assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "C3 FP32")
+
+
+def test_autotuner_choices():
+    """The tuner picks the three-stage chunk kernel for scattered columns and the
+    two-stage one for stencils, with entries per lane from the mean row length."""
+    from paper_1106_5908_gb300 import Matrix
+    H = W.hamiltonian_like(50000, seed=3)
+    info = Matrix.from_csr(H.row_ptr, H.col_idx, H.val, H.n_cols).info()
+    assert (info["family"], info["E"]) == (3, 15)
+    L3 = W.laplace3d(24)
+    info = Matrix.from_csr(L3.row_ptr, L3.col_idx, L3.val, L3.n_cols).info()
+    assert (info["family"], info["E"]) == (0, 7)
+    S27 = W.stencil27(20, seed=1)
+    info = Matrix.from_csr(S27.row_ptr, S27.col_idx, S27.val, S27.n_cols).info()
+    assert (info["family"], info["E"]) == (0, 15)
