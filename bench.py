@@ -376,30 +376,125 @@ def spot_check(A, x, y64, ys, y32):
     return out
 
 
-def measure_forms(M64, A, x, dev, form_ms, b_plain):
-    """Block vectors on the same matrix, each timed against the plain product."""
+def _time(fn, reps):
     import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_forms(M64, A, x, dev, form_ms, b_plain):
+    """The other forms, each against the plain FP64 product on the same GPU:
+    block vectors on the same matrix; mixed-precision IR-CG against FP64 CG on the
+    160^3 7-point Poisson matrix; the reverse pass on the 128^3 27-point pattern;
+    256 uneven matrices in one persistent graph launch."""
+    import torch
+    from paper_1106_5908_gb300 import Batch, Matrix, cg, ir_cg
     out = {}
-    reps = 5
     for nrhs in (4, 8, 16, 32):
         X = torch.rand(A.n_rows, nrhs, dtype=torch.float64, device=dev) * 2 - 1
         Y = torch.empty_like(X)
-        M64.spmm(X, Y)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            M64.spmm(X, Y)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = _time(lambda: M64.spmm(X, Y), 5)
         out[f"block_nrhs{nrhs}"] = {
             "ms": ms, "GBs": model.bytes_spmm(A.n_rows, A.n_cols, A.nnz, nrhs) / ms / 1e6,
             "GFLOPs": model.flops(A.nnz, nrhs) / ms / 1e6,
             "time_per_rhs_vs_plain": ms / nrhs / form_ms["plain"]}
         del X, Y
+    try:  # IR-CG on the 3D 7-point Poisson matrix
+        A3 = W.laplace3d(W.C3_GRID)
+        M3 = Matrix.from_csr(A3.row_ptr, A3.col_idx, A3.val, A3.n_cols)
+        b = torch.as_tensor(W.uniform(A3.n_rows, W.SEED_C3_B)).to(dev)
+        x3 = torch.rand(A3.n_rows, dtype=torch.float64, device=dev)
+        y3 = torch.empty_like(x3)
+        ms_plain3 = _time(lambda: M3.apply(x3, y3), 10)
+        xi, sti = ir_cg(M3, b, outer_tol=1e-12, max_outer=50, inner_tol=1e-4, max_inner=200)
+        xc, stc = cg(M3, b, tol=1e-12, max_iter=20000)
+        import oracle
+        ri = oracle.residual(*A3.astuple(), b.cpu().numpy(), xi.cpu().numpy())
+        rel_or = float(np.linalg.norm(ri) / np.linalg.norm(b.cpu().numpy()))
+        out["ir_cg_poisson160"] = {
+            "seconds": sti["seconds"], "outer": sti["outer"], "inner": sti["inner"],
+            "relres_gpu": sti["relres"], "relres_oracle": rel_or, "converged": sti["converged"],
+            "fp64_cg_seconds": stc["seconds"], "fp64_cg_iters": stc["inner"],
+            "fp64_cg_relres": stc["relres"], "time_vs_fp64_cg": sti["seconds"] / stc["seconds"],
+            "plain_f64_ms": ms_plain3,
+            "plain_f64_GBs": model.bytes_plain(A3.n_rows, A3.n_cols, A3.nnz) / ms_plain3 / 1e6}
+        del M3, b, x3, y3, xi, xc
+    except Exception as e:  # reported, not hidden
+        out["ir_cg_poisson160"] = {"error": repr(e)}
+    try:  # reverse pass on the 27-point pattern
+        A5 = W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
+        M5 = Matrix.from_csr(A5.row_ptr, A5.col_idx, A5.val, A5.n_cols)
+        x5 = torch.as_tensor(W.uniform(A5.n_cols, W.SEED_C5_X)).to(dev)
+        g5 = torch.as_tensor(W.uniform(A5.n_rows, W.SEED_C5_G)).to(dev)
+        y5 = torch.empty_like(g5)
+        ms_f = _time(lambda: M5.apply(x5, y5), 10)
+        M5.backward(g5, x5)
+        ms_b = _time(lambda: M5.backward(g5, x5), 10)
+        ms_gx = _time(lambda: M5.backward(g5, x5, need_val=False), 10)
+        out["backward_27pt128"] = {
+            "forward_ms": ms_f, "backward_ms": ms_b, "grad_x_ms": ms_gx,
+            "forward_GBs": model.bytes_plain(A5.n_rows, A5.n_cols, A5.nnz) / ms_f / 1e6,
+            "backward_GBs": model.bytes_backward(A5.n_rows, A5.n_cols, A5.nnz) / ms_b / 1e6,
+            "time_vs_plain": ms_b / ms_f}
+        del M5, x5, g5, y5
+    except Exception as e:
+        out["backward_27pt128"] = {"error": repr(e)}
+    try:  # 256 uneven matrices, one persistent launch replayed from a CUDA graph
+        sizes = W.batch_sizes(W.C4_COUNT)
+        mats, xs, ys, b_tot, nnz_tot = [], [], [], 0, 0
+        for m, n in enumerate(sizes):
+            Am = W.batch_matrix(m, int(n))
+            mats.append(Matrix.from_csr(Am.row_ptr, Am.col_idx, Am.val, Am.n_cols))
+            xs.append(torch.rand(Am.n_cols, dtype=torch.float64, device=dev))
+            ys.append(torch.empty(Am.n_rows, dtype=torch.float64, device=dev))
+            b_tot += model.bytes_plain(Am.n_rows, Am.n_cols, Am.nnz)
+            nnz_tot += Am.nnz
+        B = Batch(mats)
+        ms_b = _time(lambda: B.apply(xs, ys), 10)
+        ms_each = _time(lambda: [M.apply(xx, yy) for M, xx, yy in zip(mats, xs, ys)], 3)
+        out["batched_256"] = {
+            "ms": ms_b, "GBs": b_tot / ms_b / 1e6, "GFLOPs": 2 * nnz_tot / ms_b / 1e6,
+            "nnz": nnz_tot, "separate_launches_ms": ms_each,
+            "GBs_vs_plain": (b_tot / ms_b) / (b_plain / form_ms["plain"]), "plan": B.info()}
+        del B, mats, xs, ys
+    except Exception as e:
+        out["batched_256"] = {"error": repr(e)}
     return out
+
+
+def run_only_plain(args, local_rank):
+    """Only the plain FP64 product on the Hamiltonian-like matrix, warm-up plus K
+    launches (the case a kernel profiler captures)."""
+    import torch
+    from paper_1106_5908_gb300 import Matrix
+    from paper_1106_5908_gb300.build import build as build_lib
+    torch.cuda.set_device(local_rank)
+    build_lib()
+    A, x = c2_workload()
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+    xd = torch.as_tensor(x).cuda()
+    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        M.apply(xd, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        M.apply(xd, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"only": "plain_f64", "ms_per_launch": ms, "plan": M.info(),
+                      "GBs": model.bytes_plain(A.n_rows, A.n_cols, A.nnz) / ms / 1e6}), flush=True)
 
 
 def main():
@@ -409,6 +504,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--only", choices=("plain",), default=None,
+                    help="run only the plain FP64 product (for kernel profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -417,6 +514,9 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.only == "plain":
+        run_only_plain(args, local_rank)
         return
     if world > 1:
         import torch

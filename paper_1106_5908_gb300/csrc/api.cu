@@ -300,7 +300,7 @@ void autotune(spmv_matrix *h) {
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
-    if (h->col_random > 0.25) {
+    if (h->vk == kF64 && h->col_random > 0.25) {
         // many columns far from those of the row before: the x gathers miss L1,
         // so gather one chunk ahead (three-stage kernel)
         h->family = 3;
