@@ -263,7 +263,8 @@ spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan);
  * stats (optional HOST array of 4 doubles): outer steps, total inner iterations,
  * final relative residual ||b - A x||/||b|| (FP64, on the device), seconds.
  * Returns SPMV_ERR_NOT_CONVERGED if the outer cap is reached first.
- * Synchronises the stream (one scalar read per inner iteration). */
+ * Synchronises the stream (one scalar read-back every 8 inner iterations, so an
+ * inner solve may run up to 7 iterations past its tolerance). */
 spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_tol,
                        int32_t max_outer, double inner_tol, int32_t max_inner,
                        double *stats, void *stream);

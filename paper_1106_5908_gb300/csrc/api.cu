@@ -174,6 +174,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+constexpr int32_t kCheckEvery = 8;  // CG iterations between residual read-backs
+
 struct CgWork {
     int64_t n = 0;
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;
@@ -1233,16 +1235,20 @@ spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32
     const double bb = w.host[0];
     double rho = bb;
     int32_t it = 0;
+    // the residual is read back every kCheckEvery iterations (one host round trip
+    // per check, not per iteration); CG may run up to kCheckEvery-1 extra steps
     while (it < max_iter && std::sqrt(rho) > tol * std::sqrt(bb)) {
         st = apply_impl(h, 1.0, w.p64, kF64, 0.0, w.q64, kF64, s);
         if (st != SPMV_OK) return st;
         CK(cg_dot(w.p64, kF64, w.q64, kF64, n, w.partials, w.sc, kOpAlpha, 0, s));
         CK(cg_update64(x, w.r64, w.p64, w.q64, n, w.partials, w.sc, s));
         CK(cg_direction(w.p64, w.r64, kF64, w.sc, n, s));
-        CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rho = w.host[0];
         ++it;
+        if (it % kCheckEvery == 0 || it == max_iter) {
+            CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rho = w.host[0];
+        }
     }
     // true residual in FP64
     CK(cudaMemcpyAsync(w.r64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
@@ -1313,10 +1319,12 @@ spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_t
             CK(cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, s));
             CK(cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, s));
             CK(cg_direction(w.p32, w.r32, kF32, w.sc, n, s));
-            CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            rho = w.host[0];
             ++it;
+            if (it % kCheckEvery == 0 || it == max_inner) {
+                CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                rho = w.host[0];
+            }
         }
         inner_total += it;
         // update (FP64): x += ||r|| d

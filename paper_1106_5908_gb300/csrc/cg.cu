@@ -49,11 +49,11 @@ __global__ void __launch_bounds__(kDotThreads) k_reduce(const double *__restrict
     if (threadIdx.x == 0) {
         if (op == kOpStore) {
             sc[dst] = t;
-        } else if (op == kOpAlpha) {  // t = p.q
+        } else if (op == kOpAlpha) {  // t = p.q; a zero direction (converged) takes no step
             sc[kScPQ] = t;
-            sc[kScAlpha] = sc[kScRho] / t;
+            sc[kScAlpha] = (t != 0.0) ? sc[kScRho] / t : 0.0;
         } else if (op == kOpBeta) {   // t = r_new.r_new
-            sc[kScBeta] = t / sc[kScRho];
+            sc[kScBeta] = (sc[kScRho] != 0.0) ? t / sc[kScRho] : 0.0;
             sc[kScRho] = t;
         }
     }
