@@ -287,9 +287,8 @@ k_pipe3(const WarpParams p) {
         phase ^= 1u << s;
         return __all_sync(0xffffffffu, ok);
     };
-    // Gathers and row bookkeeping of the chunk staged in s (regular chunks only);
-    // done one chunk ahead so both overlap the FMA chains of the current chunk.
-    auto prepare = [&](int cc, int s, XT (&xv)[E], LaneMeta &mt) {
+    // gathers of the chunk staged in s (regular chunks only)
+    auto gather = [&](int cc, int s, XT (&xv)[E]) {
         const unsigned char *st = ws + s * L::stage;
         const ChunkDesc d = *reinterpret_cast<const ChunkDesc *>(st + L::off_desc);
 #pragma unroll
@@ -298,7 +297,6 @@ k_pipe3(const WarpParams p) {
         const MatRef m = mat_of(cc);
         const XT *__restrict__ x = static_cast<const XT *>(m.x);
         const int32_t *sc = reinterpret_cast<const int32_t *>(st + L::off_col);
-        const uint32_t *smk = reinterpret_cast<const uint32_t *>(st + L::off_mask);
         const int base = d.k0 & ~3;
         const int off = lane * E;
         const int lo = max(0, d.k0 - base - off);
@@ -306,15 +304,9 @@ k_pipe3(const WarpParams p) {
 #pragma unroll
         for (int e = 0; e < E; ++e)
             if (e >= lo && e < hi) xv[e] = __ldg(x + sc[off + e]);
-        const int w0 = off >> 5, sh = off & 31;
-        const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
-        const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
-        const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
-        const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
-        mt = lane_meta(mbits, lo, hi, ends, d.r0, lane);
     };
 
-    // prologue: chunks c0 and c0+nwarps in flight, chunk c0 prepared
+    // prologue: chunks c0 and c0+nwarps in flight, gathers of c0 issued
     ChunkDesc dnext{};
     if (lane == 0) {
         issue(c0, p.chunks[c0], 0);
@@ -324,12 +316,11 @@ k_pipe3(const WarpParams p) {
         }
     }
     XT xcur[E];
-    LaneMeta mcur{};
     if (!wait_stage(0)) {
         if (lane == 0) set_error(p.err, kDevErrTimeout);
         return;
     }
-    prepare(c0, 0, xcur, mcur);
+    gather(c0, 0, xcur);
 
     int s = 0;
     for (int c = c0; c < p.n_chunks; c += nwarps) {
@@ -340,7 +331,6 @@ k_pipe3(const WarpParams p) {
             if (c2 + nwarps < p.n_chunks) dnext = p.chunks[c2 + nwarps];
         }
         XT xnext[E];
-        LaneMeta mnext{};
 #pragma unroll
         for (int e = 0; e < E; ++e) xnext[e] = XT(0);
         if (c1 < p.n_chunks) {
@@ -348,9 +338,9 @@ k_pipe3(const WarpParams p) {
                 if (lane == 0) set_error(p.err, kDevErrTimeout);
                 return;
             }
-            prepare(c1, s1, xnext, mnext);
+            gather(c1, s1, xnext);
         }
-        // ---- chunk c (staged in s, prepared in xcur/mcur) ---------------------
+        // ---- chunk c (staged in s, gathers in xcur) --------------------------
         const unsigned char *st = ws + s * L::stage;
         const ChunkDesc d = *reinterpret_cast<const ChunkDesc *>(st + L::off_desc);
         const MatRef m = mat_of(c);
@@ -364,14 +354,20 @@ k_pipe3(const WarpParams p) {
             rows_per_lane<VT, XT, YT, ACC, false>(m, r0, r1, x, y, alpha, beta, plain, lane);
         } else {
             const VS *sv = reinterpret_cast<const VS *>(st + L::off_vs);
+            const uint32_t *smk = reinterpret_cast<const uint32_t *>(st + L::off_mask);
             const int base = d.k0 & ~3;
             const int off = lane * E;
             const int lo = max(0, d.k0 - base - off);
             const int hi = min(E, d.k1 - base - off);
+            const int w0 = off >> 5, sh = off & 31;
+            const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
+            const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
             VT vals[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) vals[e] = (e >= lo && e < hi) ? sv[off + e] : VT(0);
-            lane_rows<E, VT, XT, ACC>(vals, xcur, mcur, r0, srow);
+            const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
+            const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
+            chunk_lane<E, VT, XT, ACC>(vals, xcur, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
             for (int q = lane; q < r1 - r0; q += 32)
                 store_row(y, r0 + q, srow[q].get(), alpha, beta, plain, m.rmap);
@@ -379,7 +375,6 @@ k_pipe3(const WarpParams p) {
         __syncwarp();  // stage s and the row buffer are free again
 #pragma unroll
         for (int e = 0; e < E; ++e) xcur[e] = xnext[e];
-        mcur = mnext;
         s = s1;
     }
 }

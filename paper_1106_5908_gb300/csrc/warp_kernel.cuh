@@ -154,16 +154,9 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
 // is known to have started in this lane, so the last store of a row is its full
 // sum.  The part of the first row that started in an earlier lane is combined in
 // lane order with the carries of those lanes (one FP64 add per crossing).
-struct LaneMeta {
-    int row;         // row of the lane's first valid slot
-    uint32_t flush;  // bit e: a row starts in slot e (after the first valid slot)
-    bool started;    // the first row starts in this lane
-    bool active;     // the lane has valid slots
-    bool ends;       // the lane's last row ends with its slots
-};
-
-// Row bookkeeping of one lane (needs the whole warp: prefix over lanes).
-__device__ __forceinline__ LaneMeta lane_meta(uint32_t mbits, int lo, int hi, bool ends, int r0, int lane) {
+template <int E, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
+                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
     const int cnt = __popc(mbits);
     int pre = cnt;
 #pragma unroll
@@ -172,33 +165,16 @@ __device__ __forceinline__ LaneMeta lane_meta(uint32_t mbits, int lo, int hi, bo
         if (lane >= o) pre += t;
     }
     pre -= cnt;  // row starts in the chunk before this lane's slots
-    LaneMeta mt;
-    mt.active = lo < hi;
-    mt.started = mt.active && ((mbits >> lo) & 1u);
-    mt.row = r0 + pre + (mt.started ? 1 : 0) - 1;
-    mt.flush = mt.active ? (mbits & ~(1u << lo)) : 0u;
-    mt.ends = ends;
-    return mt;
-}
-
-// One lane's share of a regular chunk.  vals/xv hold the lane's E slots (zero in
-// slots outside its valid range).  The FMA chain restarts at every row start (a
-// register select, no branch) and the running sum of the current row is stored
-// to the row buffer after every entry once the row is known to have started in
-// this lane, so the last store of a row is its full sum.  The part of the first
-// row that started in an earlier lane is combined in lane order with the carries
-// of those lanes (one FP64 add per crossing).
-template <int E, typename VT, typename XT, typename ACC>
-__device__ __forceinline__ void lane_rows(const VT (&vals)[E], const XT (&xv)[E], const LaneMeta &mt,
-                                          int r0, ACC *srow) {
-    int row = mt.row;
-    const int first_row = mt.row;
-    const uint32_t flush = mt.flush;
+    const bool active = lo < hi;
+    const bool starts_first = active && ((mbits >> lo) & 1u);
+    int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
+    const int first_row = row;
+    const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
     ACC acc;
     acc.zero();
     ACC pend;
     pend.zero();
-    bool started = mt.started;
+    bool started = starts_first;
     bool has_pend = false;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -212,11 +188,11 @@ __device__ __forceinline__ void lane_rows(const VT (&vals)[E], const XT (&xv)[E]
         acc.fma(vals[e], xv[e]);
         if (started) srow[row - r0] = acc;
     }
-    if (mt.active && !started && mt.ends) {
+    if (active && !started && ends) {
         pend = acc;
         has_pend = true;
     }
-    const bool carry = mt.active && !mt.ends;
+    const bool carry = active && !ends;
     const bool through = carry && !started;  // the lane's slots lie inside one row
     ACC tot = pend;
     int dist = 1;
@@ -233,13 +209,6 @@ __device__ __forceinline__ void lane_rows(const VT (&vals)[E], const XT (&xv)[E]
         ++dist;
     }
     if (has_pend) srow[first_row - r0] = tot;
-}
-
-template <int E, typename VT, typename XT, typename ACC>
-__device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
-                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
-    const LaneMeta mt = lane_meta(mbits, lo, hi, ends, r0, lane);
-    lane_rows<E, VT, XT, ACC>(vals, xv, mt, r0, srow);
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
