@@ -112,6 +112,26 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time); the only
+    cross-rank operation of the benchmark (replicas share no data)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(bytes_per_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Algorithmic GB/s of the whole job: the bytes every rank moved over the
+    slowest rank's time."""
+    return bytes_per_step * steps * world / (max_ms / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ workload
 
 def c2_workload():
@@ -263,10 +283,7 @@ def run_ours(args, rank, world, local_rank):
     ms = t_start.elapsed_time(t_end)
     form_ms = {k: float(np.mean([ev[k][i].elapsed_time(ev_end[k][i]) for i in range(K)]))
                for k in ev}
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # ---- end to end through the public API with host buffers ---------------
     xh = torch.as_tensor(x).pin_memory()
@@ -296,10 +313,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(s1)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
 
     # correctness spot check of the timed outputs (sampled rows against the oracle)
     check = spot_check(A, x, y64, ys, y32)
@@ -314,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = b_plain / avg_plain_s / 1e9
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_hash"] == kernel_hash() else None
     cpu = cpu_baseline(A, x, b_plain) if world == 1 or rank == 0 else None
-    value = b_step * K * world / (ms / 1e3) / 1e9
+    value = whole_job_value(b_step, K, world, ms)
     info = M64.info()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -346,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
                         "achieved_bytes_per_flop_alg": b_plain / model.flops(nnz)},
         "check": check,
         "cpu_baseline": cpu,
-        "e2e": {"value": b_step * K * world / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+        "e2e": {"value": whole_job_value(b_step, K, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * n + 4 * n, "d2h_bytes_per_step": 8 * n + 8 * n + 4 * n,
                 "ms_per_step": e2e_ms / K},
         "gpu_launches": 5 * K,
