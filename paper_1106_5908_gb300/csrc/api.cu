@@ -182,6 +182,13 @@ struct CgWork {
     float *r32 = nullptr, *d32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     double *sc = nullptr, *partials = nullptr;
     double *host = nullptr;  // pinned scalars
+    // kCheckEvery CG iterations captured once and replayed (host launch overhead
+    // paid once per block); re-captured when the operands or the plan change
+    cudaGraphExec_t inner32 = nullptr;  // FP32 inner CG of the IR solver
+    int64_t inner32_key = -1;
+    cudaGraphExec_t cg64 = nullptr;     // FP64 CG (x is the caller's pointer)
+    const void *cg64_x = nullptr;
+    int64_t cg64_key = -1;
 };
 
 struct spmv_matrix {
@@ -397,6 +404,8 @@ spmv_status upload_matrix(spmv_matrix *h, const int32_t *row_ptr, const int32_t 
 }
 
 void destroy_cg(CgWork &w) {
+    if (w.inner32) cudaGraphExecDestroy(w.inner32);
+    if (w.cg64) cudaGraphExecDestroy(w.cg64);
     cudaFree(w.r64); cudaFree(w.p64); cudaFree(w.q64);
     cudaFree(w.r32); cudaFree(w.d32); cudaFree(w.p32); cudaFree(w.q32);
     cudaFree(w.sc); cudaFree(w.partials);
@@ -608,6 +617,44 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Everything an apply needs (chunk tables) is built before a capture, so no
+// allocation happens while a stream is being captured.
+static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    if (h->family == 0 || h->family == 3 || h->d_rmap) {
+        int E = h->E;
+        WarpOps ops;
+        const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
+        if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) E = 16;
+        return get_chunks(h, E, false) ? SPMV_OK : SPMV_ERR_ALLOC;
+    }
+    if (h->family == 2) {
+        const int E = pick_E(h->vk, xk, yk, acc, h->E);
+        TileRun run;
+        return prepare_run(h, xk, yk, 1, E, false, &run);
+    }
+    return SPMV_OK;
+}
+
+// Capture `body` (which enqueues kernels on the given stream) into a graph.
+template <typename F>
+static spmv_status capture_graph(F body, cudaGraphExec_t *exec) {
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    spmv_status st = SPMV_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = body(cap);
+        e = cudaStreamEndCapture(cap, &g);
+    }
+    if (e == cudaSuccess && st == SPMV_OK) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (st != SPMV_OK) return st;
+    return e == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+}
 
 extern "C" {
 
@@ -1038,13 +1085,13 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         if (ops.launch(wp, ct->n, s) != cudaSuccess) return SPMV_ERR_CUDA;
     }
     if (grad_val && h->nnz > 0) {
-        TileOps ops;
-        const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-        if (!tile_ops(h->vk, h->vk, h->vk, acc, 1, 15, false, false, &ops)) return SPMV_ERR_UNSUPPORTED;
-        const TileCfg c = ops.cfg();
-        TileTable *tt = get_table(h, c.cap, c.rowcap, false);
-        if (!tt) return SPMV_ERR_ALLOC;
-        if (launch_grad_val(h->d_rp, h->d_col, tt->d, tt->n, c.cap, h->vk, g, x, alpha, grad_val, s) != cudaSuccess)
+        // the forward plan's chunks (any E): rows from the row-start bitmasks
+        const int E = (h->E == 7 || h->E == 8 || h->E == 11 || h->E == 15 || h->E == 16) ? h->E : 15;
+        ChunkTable *ct = get_chunks(h, E, false);
+        if (!ct) return SPMV_ERR_ALLOC;
+        const int mwp = ((E + 3) / 4) * 4;
+        if (launch_grad_val_chunks(h->d_rp, h->d_col, ct->d, ct->masks, mwp, ct->n, h->vk, g, x, alpha,
+                                   grad_val, s) != cudaSuccess)
             return SPMV_ERR_CUDA;
     }
     return SPMV_OK;
@@ -1237,18 +1284,46 @@ spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32
     int32_t it = 0;
     // the residual is read back every kCheckEvery iterations (one host round trip
     // per check, not per iteration); CG may run up to kCheckEvery-1 extra steps
+    auto iter = [&](cudaStream_t cs) -> spmv_status {
+        spmv_status s2 = apply_impl(h, 1.0, w.p64, kF64, 0.0, w.q64, kF64, cs);
+        if (s2 != SPMV_OK) return s2;
+        if (cg_dot(w.p64, kF64, w.q64, kF64, n, w.partials, w.sc, kOpAlpha, 0, cs) != cudaSuccess ||
+            cg_update64(x, w.r64, w.p64, w.q64, n, w.partials, w.sc, cs) != cudaSuccess ||
+            cg_direction(w.p64, w.r64, kF64, w.sc, n, cs) != cudaSuccess)
+            return SPMV_ERR_CUDA;
+        return SPMV_OK;
+    };
+    const int64_t key = static_cast<int64_t>(h->family) * 1000 + h->E;
     while (it < max_iter && std::sqrt(rho) > tol * std::sqrt(bb)) {
-        st = apply_impl(h, 1.0, w.p64, kF64, 0.0, w.q64, kF64, s);
-        if (st != SPMV_OK) return st;
-        CK(cg_dot(w.p64, kF64, w.q64, kF64, n, w.partials, w.sc, kOpAlpha, 0, s));
-        CK(cg_update64(x, w.r64, w.p64, w.q64, n, w.partials, w.sc, s));
-        CK(cg_direction(w.p64, w.r64, kF64, w.sc, n, s));
-        ++it;
-        if (it % kCheckEvery == 0 || it == max_iter) {
-            CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            rho = w.host[0];
+        if (max_iter - it >= kCheckEvery && w.cg64 && w.cg64_key == key && w.cg64_x == x) {
+            CK(cudaGraphLaunch(w.cg64, s));
+            it += kCheckEvery;
+        } else {
+            const int blk = std::min<int32_t>(kCheckEvery, max_iter - it);
+            for (int j = 0; j < blk; ++j) {
+                st = iter(s);
+                if (st != SPMV_OK) return st;
+            }
+            it += blk;
+            if (blk == kCheckEvery && (!w.cg64 || w.cg64_key != key || w.cg64_x != x)) {
+                if (w.cg64) { cudaGraphExecDestroy(w.cg64); w.cg64 = nullptr; }
+                st = ready_for_capture(h, kF64, kF64);
+                if (st == SPMV_OK)
+                    st = capture_graph([&](cudaStream_t cs) -> spmv_status {
+                        for (int j = 0; j < kCheckEvery; ++j) {
+                            const spmv_status s3 = iter(cs);
+                            if (s3 != SPMV_OK) return s3;
+                        }
+                        return SPMV_OK;
+                    }, &w.cg64);
+                if (st != SPMV_OK) return st;
+                w.cg64_key = key;
+                w.cg64_x = x;
+            }
         }
+        CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rho = w.host[0];
     }
     // true residual in FP64
     CK(cudaMemcpyAsync(w.r64, b, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
@@ -1313,18 +1388,47 @@ spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_t
         const double rho0 = w.host[0];
         double rho = rho0;
         int32_t it = 0;
+        auto inner_iter = [&](cudaStream_t cs) -> spmv_status {
+            spmv_status s2 = apply_impl(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, cs);
+            if (s2 != SPMV_OK) return s2;
+            if (cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, cs) != cudaSuccess ||
+                cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, cs) != cudaSuccess ||
+                cg_direction(w.p32, w.r32, kF32, w.sc, n, cs) != cudaSuccess)
+                return SPMV_ERR_CUDA;
+            return SPMV_OK;
+        };
+        const int64_t key = static_cast<int64_t>(A32->family) * 1000 + A32->E;
         while (it < max_inner && std::sqrt(rho) > inner_tol * std::sqrt(rho0)) {
-            st = apply_impl(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, s);
-            if (st != SPMV_OK) return st;
-            CK(cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, s));
-            CK(cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, s));
-            CK(cg_direction(w.p32, w.r32, kF32, w.sc, n, s));
-            ++it;
-            if (it % kCheckEvery == 0 || it == max_inner) {
-                CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-                rho = w.host[0];
+            if (max_inner - it >= kCheckEvery && w.inner32 && w.inner32_key == key) {
+                CK(cudaGraphLaunch(w.inner32, s));
+                it += kCheckEvery;
+            } else {
+                // plain launches (also the first block, which prepares every
+                // kernel before the block is captured)
+                const int blk = std::min<int32_t>(kCheckEvery, max_inner - it);
+                for (int j = 0; j < blk; ++j) {
+                    st = inner_iter(s);
+                    if (st != SPMV_OK) return st;
+                }
+                it += blk;
+                if (blk == kCheckEvery && (!w.inner32 || w.inner32_key != key)) {
+                    if (w.inner32) { cudaGraphExecDestroy(w.inner32); w.inner32 = nullptr; }
+                    st = ready_for_capture(A32, kF32, kF32);
+                    if (st == SPMV_OK)
+                        st = capture_graph([&](cudaStream_t cs) -> spmv_status {
+                            for (int j = 0; j < kCheckEvery; ++j) {
+                                const spmv_status s3 = inner_iter(cs);
+                                if (s3 != SPMV_OK) return s3;
+                            }
+                            return SPMV_OK;
+                        }, &w.inner32);
+                    if (st != SPMV_OK) return st;
+                    w.inner32_key = key;
+                }
             }
+            CK(cudaMemcpyAsync(w.host, w.sc + kScRho, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            rho = w.host[0];
         }
         inner_total += it;
         // update (FP64): x += ||r|| d

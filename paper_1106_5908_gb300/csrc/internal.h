@@ -91,10 +91,12 @@ cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
                           cudaStream_t s);
 
-// grad_val[k] = alpha * g[row(k)] * x[col[k]] over the tiles of A.
-cudaError_t launch_grad_val(const int32_t *rp, const int32_t *col, const TileDesc *tiles,
-                            int32_t n_tiles, int32_t cap, int vk, const void *g, const void *x,
-                            double alpha, void *grad_val, cudaStream_t s);
+// grad_val over the warp chunks of A (ChunkDesc table + row-start bitmasks with
+// mwp words per chunk).
+cudaError_t launch_grad_val_chunks(const int32_t *rp, const int32_t *col, const void *chunks,
+                                   const uint32_t *masks, int mwp, int32_t n_chunks, int vk,
+                                   const void *g, const void *x, double alpha, void *grad_val,
+                                   cudaStream_t s);
 
 // Transposed structure: counts, exclusive scan, fill, per-row ordering.
 cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,

@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "warp_kernel.cuh"
 
 namespace spmv {
 
@@ -113,73 +114,70 @@ cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// grad_val[k] = alpha * g[row(k)] * x[col[k]].  One CTA per tile of A; each
-// thread owns E consecutive entries of a chunk (row tracked as in the tile
-// kernel, alpha*g[row] formed once per row), results are staged in shared
-// memory and written out contiguously.
-// ---------------------------------------------------------------------------
+// grad_val over the warp chunks of A: lanes take 32 consecutive entries at a
+// time (coalesced column loads and gradient stores); the row of each entry is the
+// chunk's first row plus the row starts (bits of the chunk's bitmask) up to it.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_grad_val(const int32_t *__restrict__ rp,
-                                                  const int32_t *__restrict__ col,
-                                                  const TileDesc *__restrict__ tiles,
-                                                  const VT *__restrict__ g,
-                                                  const VT *__restrict__ x, double alpha,
-                                                  VT *__restrict__ gv) {
-    constexpr int NT = 256, E = 15, CH = NT * E;
-    __shared__ VT s_out[CH];
-    __shared__ int32_t s_col[CH];
-    const TileDesc d = tiles[blockIdx.x];
-    const int tid = threadIdx.x;
-    for (int cb = d.k0; cb < d.k1; cb += CH) {
-        const int n = min(CH, d.k1 - cb);
-        for (int j = tid; j < n; j += NT) s_col[j] = __ldg(col + cb + j);
-        __syncthreads();
-        const int jb = tid * E;
-        if (jb < n) {
-            const int kb = cb + jb;
-            const int ke = min(kb + E, d.k1);
-            int lo = d.r0, hi = d.r1 - 1;  // largest row with row_ptr[row] <= kb
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(rp + mid) <= kb) lo = mid;
-                else hi = mid - 1;
-            }
-            int row = lo;
-            int next = __ldg(rp + row + 1);
-            VT scale = static_cast<VT>(static_cast<VT>(alpha) * __ldg(g + row));
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int k = kb + e;
-                if (k < ke) {
-                    while (k >= next) {
-                        ++row;
-                        next = __ldg(rp + row + 1);
-                        scale = static_cast<VT>(static_cast<VT>(alpha) * __ldg(g + row));
-                    }
-                    s_out[jb + e] = scale * __ldg(x + s_col[jb + e]);
-                }
-            }
+__global__ void __launch_bounds__(256) k_grad_val_chunks(const int32_t *__restrict__ rp,
+                                                         const int32_t *__restrict__ col,
+                                                         const ChunkDesc *__restrict__ chunks,
+                                                         const uint32_t *__restrict__ masks, int mwp,
+                                                         int32_t n_chunks, const VT *__restrict__ g,
+                                                         const VT *__restrict__ x, double alpha,
+                                                         VT *__restrict__ gv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    if (w >= n_chunks) return;
+    const ChunkDesc d = chunks[w];
+    const int r0 = d.r0;
+    const int r1 = d.r1f & kChunkRowMask;
+    const bool scaled = (alpha != 1.0);
+    const VT a = static_cast<VT>(alpha);
+    if (d.r1f & kChunkLong) {
+        const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r0)) : __ldg(g + r0);
+        for (int k = d.k0 + lane; k < d.k1; k += 32) gv[k] = gr * __ldg(x + __ldg(col + k));
+        return;
+    }
+    if (d.r1f & kChunkEmpty) {
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r)) : __ldg(g + r);
+            const int kb = __ldg(rp + r), ke = __ldg(rp + r + 1);
+            for (int k = kb; k < ke; ++k) gv[k] = gr * __ldg(x + __ldg(col + k));
         }
-        __syncthreads();
-        for (int j = tid; j < n; j += NT) gv[cb + j] = s_out[j];
-        __syncthreads();
+        return;
+    }
+    const int base = d.k0 & ~3;
+    int rows_before = 0;  // row starts in the chunk's earlier words
+    const uint32_t below = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+    for (int wd = 0; base + 32 * wd < d.k1; ++wd) {
+        const uint32_t word = __ldg(masks + w * mwp + wd);
+        const int k = base + 32 * wd + lane;
+        if (k >= d.k0 && k < d.k1) {
+            const int row = r0 + rows_before + __popc(word & below) - 1;
+            const VT gr = scaled ? static_cast<VT>(a * __ldg(g + row)) : __ldg(g + row);
+            gv[k] = gr * __ldg(x + __ldg(col + k));
+        }
+        rows_before += __popc(word);
     }
 }
 
-cudaError_t launch_grad_val(const int32_t *rp, const int32_t *col, const TileDesc *tiles,
-                            int32_t n_tiles, int32_t cap, int vk, const void *g, const void *x,
-                            double alpha, void *grad_val, cudaStream_t s) {
-    (void)cap;
-    if (n_tiles <= 0) return cudaSuccess;
+cudaError_t launch_grad_val_chunks(const int32_t *rp, const int32_t *col, const void *chunks,
+                                   const uint32_t *masks, int mwp, int32_t n_chunks, int vk,
+                                   const void *g, const void *x, double alpha, void *grad_val,
+                                   cudaStream_t s) {
+    if (n_chunks <= 0) return cudaSuccess;
+    const int grid = (n_chunks + 7) / 8;
+    const ChunkDesc *c = static_cast<const ChunkDesc *>(chunks);
     if (vk == kF64)
-        k_grad_val<double><<<n_tiles, 256, 0, s>>>(rp, col, tiles, static_cast<const double *>(g),
-                                                   static_cast<const double *>(x), alpha,
-                                                   static_cast<double *>(grad_val));
+        k_grad_val_chunks<double><<<grid, 256, 0, s>>>(rp, col, c, masks, mwp, n_chunks,
+                                                       static_cast<const double *>(g),
+                                                       static_cast<const double *>(x), alpha,
+                                                       static_cast<double *>(grad_val));
     else
-        k_grad_val<float><<<n_tiles, 256, 0, s>>>(rp, col, tiles, static_cast<const float *>(g),
-                                                  static_cast<const float *>(x), alpha,
-                                                  static_cast<float *>(grad_val));
+        k_grad_val_chunks<float><<<grid, 256, 0, s>>>(rp, col, c, masks, mwp, n_chunks,
+                                                      static_cast<const float *>(g),
+                                                      static_cast<const float *>(x), alpha,
+                                                      static_cast<float *>(grad_val));
     return cudaGetLastError();
 }
 
