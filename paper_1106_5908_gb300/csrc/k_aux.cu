@@ -146,18 +146,37 @@ __global__ void __launch_bounds__(256) k_grad_val_chunks(const int32_t *__restri
         }
         return;
     }
+    // all loads of the chunk are issued before any use (up to 16 words of 32)
+    constexpr int MAXW = 16;
     const int base = d.k0 & ~3;
-    int rows_before = 0;  // row starts in the chunk's earlier words
     const uint32_t below = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
-    for (int wd = 0; base + 32 * wd < d.k1; ++wd) {
-        const uint32_t word = __ldg(masks + w * mwp + wd);
+    uint32_t words[MAXW];
+    int32_t cc[MAXW];
+#pragma unroll
+    for (int wd = 0; wd < MAXW; ++wd) {
         const int k = base + 32 * wd + lane;
-        if (k >= d.k0 && k < d.k1) {
-            const int row = r0 + rows_before + __popc(word & below) - 1;
-            const VT gr = scaled ? static_cast<VT>(a * __ldg(g + row)) : __ldg(g + row);
-            gv[k] = gr * __ldg(x + __ldg(col + k));
+        words[wd] = (wd < mwp) ? __ldg(masks + w * mwp + wd) : 0u;
+        cc[wd] = (k >= d.k0 && k < d.k1) ? __ldg(col + k) : -1;
+    }
+    VT xv[MAXW], gr[MAXW];
+    int rows_before = 0;  // row starts in the chunk's earlier words
+#pragma unroll
+    for (int wd = 0; wd < MAXW; ++wd) {
+        const int row = r0 + rows_before + __popc(words[wd] & below) - 1;
+        xv[wd] = VT(0);
+        gr[wd] = VT(0);
+        if (cc[wd] >= 0) {
+            xv[wd] = __ldg(x + cc[wd]);
+            gr[wd] = __ldg(g + row);
         }
-        rows_before += __popc(word);
+        rows_before += __popc(words[wd]);
+    }
+#pragma unroll
+    for (int wd = 0; wd < MAXW; ++wd) {
+        if (cc[wd] >= 0) {
+            const VT gg = scaled ? static_cast<VT>(a * gr[wd]) : gr[wd];
+            gv[base + 32 * wd + lane] = gg * xv[wd];
+        }
     }
 }
 
