@@ -303,13 +303,21 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 // the extra warps in flight, long rows from fewer rows cut by lane boundaries
 // (measured on the 7-point, Hamiltonian-like and 27-point matrices).  The
 // row-vector kernel's lanes per row T (family 1) is the power of two nearest
-// half the mean row length, used when chosen explicitly.
+// half the mean row length, used when chosen explicitly.  FP32 storage halves
+// the bytes per chunk, so its chunks take 15 entries per lane unless the
+// columns are scattered, where 7 (more warps, more gathers in flight) wins
+// (measured: 7-point 68 vs 78 us, 27-point 117 vs 173 us, Hamiltonian-like
+// 165 vs 192 us).
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
-    if (h->vk == kF64 && h->col_random > 0.25) {
+    const bool scattered = h->col_random > 0.25;
+    if (h->vk == kF32) {
+        h->family = 0;
+        h->E = scattered ? 7 : 15;
+    } else if (scattered) {
         // many columns far from those of the row before: the x gathers miss L1,
         // so gather one chunk ahead (three-stage kernel)
         h->family = 3;

@@ -2,6 +2,7 @@
 // products with a deterministic two-stage reduction, fused CG updates in FP32
 // (inner solver) and FP64 (outer residual, update, and the FP64 reference CG).
 #include <algorithm>
+#include <cstdint>
 
 #include "common.cuh"
 #include "cg.h"
@@ -36,6 +37,50 @@ __global__ void __launch_bounds__(kDotThreads) k_dot(const TA *__restrict__ a,
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
         acc = fma(widen(a[i]), widen(b[i]), acc);
     const double t = block_sum(acc, s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// Vectorised variants for 16-byte aligned operands: four floats (or two
+// doubles) per load and independent accumulators, so each thread keeps several
+// loads in flight; the tail is handled element by element.  FP32 operands are
+// accumulated as float-float pairs (exact products, two-sum), which keeps the
+// FP64 pipe out of the loop; each thread's pairs are summed in FP64.
+__global__ void __launch_bounds__(kDotThreads) k_dot_f32v(const float4 *__restrict__ a,
+                                                          const float4 *__restrict__ b, int64_t n4,
+                                                          const float *__restrict__ at,
+                                                          const float *__restrict__ bt, int tail,
+                                                          double *__restrict__ partials) {
+    __shared__ double s_red[32];
+    AccFF c0, c1, c2, c3;
+    c0.zero(); c1.zero(); c2.zero(); c3.zero();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 u = __ldg(a + i), v = __ldg(b + i);
+        c0.fma(u.x, v.x);
+        c1.fma(u.y, v.y);
+        c2.fma(u.z, v.z);
+        c3.fma(u.w, v.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) c0.fma(at[threadIdx.x], bt[threadIdx.x]);
+    const double t = block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kDotThreads) k_dot_f64v(const double2 *__restrict__ a,
+                                                          const double2 *__restrict__ b, int64_t n2,
+                                                          const double *__restrict__ at,
+                                                          const double *__restrict__ bt, int tail,
+                                                          double *__restrict__ partials) {
+    __shared__ double s_red[32];
+    double c0 = 0.0, c1 = 0.0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        const double2 u = __ldg(a + i), v = __ldg(b + i);
+        c0 = fma(u.x, v.x, c0);
+        c1 = fma(u.y, v.y, c1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) c0 = fma(at[threadIdx.x], bt[threadIdx.x], c0);
+    const double t = block_sum(c0 + c1, s_red);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
@@ -79,6 +124,61 @@ __global__ void __launch_bounds__(kDotThreads) k_update32(float *__restrict__ d,
     }
     const double t = block_sum(acc, s_red);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kDotThreads) k_update32v(float4 *__restrict__ d, float4 *__restrict__ r,
+                                                           const float4 *__restrict__ p,
+                                                           const float4 *__restrict__ q,
+                                                           const double *__restrict__ sc, int64_t n4,
+                                                           float *__restrict__ dt, float *__restrict__ rt,
+                                                           const float *__restrict__ pt,
+                                                           const float *__restrict__ qt, int tail,
+                                                           double *__restrict__ partials) {
+    __shared__ double s_red[32];
+    const float a = __double2float_rn(sc[kScAlpha]);
+    AccFF c0, c1, c2, c3;
+    c0.zero(); c1.zero(); c2.zero(); c3.zero();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 pv = p[i], qv = q[i];
+        float4 dv = d[i], rv = r[i];
+        dv.x = fmaf(a, pv.x, dv.x); dv.y = fmaf(a, pv.y, dv.y);
+        dv.z = fmaf(a, pv.z, dv.z); dv.w = fmaf(a, pv.w, dv.w);
+        rv.x = fmaf(-a, qv.x, rv.x); rv.y = fmaf(-a, qv.y, rv.y);
+        rv.z = fmaf(-a, qv.z, rv.z); rv.w = fmaf(-a, qv.w, rv.w);
+        d[i] = dv;
+        r[i] = rv;
+        c0.fma(rv.x, rv.x);
+        c1.fma(rv.y, rv.y);
+        c2.fma(rv.z, rv.z);
+        c3.fma(rv.w, rv.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) {
+        const int j = threadIdx.x;
+        dt[j] = fmaf(a, pt[j], dt[j]);
+        const float ri = fmaf(-a, qt[j], rt[j]);
+        rt[j] = ri;
+        c0.fma(ri, ri);
+    }
+    const double t = block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kDotThreads) k_direction32v(float4 *__restrict__ p,
+                                                              const float4 *__restrict__ r,
+                                                              const double *__restrict__ sc, int64_t n4,
+                                                              float *__restrict__ pt,
+                                                              const float *__restrict__ rt, int tail) {
+    const float b = static_cast<float>(sc[kScBeta]);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 rv = r[i];
+        float4 pv = p[i];
+        pv.x = fmaf(b, pv.x, rv.x); pv.y = fmaf(b, pv.y, rv.y);
+        pv.z = fmaf(b, pv.z, rv.z); pv.w = fmaf(b, pv.w, rv.w);
+        p[i] = pv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) pt[threadIdx.x] = fmaf(b, pt[threadIdx.x], rt[threadIdx.x]);
 }
 
 // FP64 update of the reference CG: x += a*p, r -= a*q, partial sums of r.r.
@@ -133,33 +233,69 @@ static int vec_grid(int64_t n) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 4LL * sms)));
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 16LL * sms)));
 }
 
 int cg_partials_len() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return 4 * sms;
+    return 16 * sms;
 }
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 cudaError_t cg_dot(const void *a, int ak, const void *b, int bk, int64_t n, double *partials,
                    double *sc, int op, int dst, cudaStream_t s) {
-    const int grid = vec_grid(n);
-    if (ak == kF64 && bk == kF64)
-        k_dot<double, double><<<grid, kDotThreads, 0, s>>>(static_cast<const double *>(a), static_cast<const double *>(b), n, partials);
-    else if (ak == kF32 && bk == kF32)
-        k_dot<float, float><<<grid, kDotThreads, 0, s>>>(static_cast<const float *>(a), static_cast<const float *>(b), n, partials);
-    else
+    int grid;
+    if (ak == kF64 && bk == kF64) {
+        const double *ad = static_cast<const double *>(a), *bd = static_cast<const double *>(b);
+        if (aligned16(a) && aligned16(b)) {
+            const int64_t n2 = n / 2;
+            grid = vec_grid(n2);
+            k_dot_f64v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<const double2 *>(ad),
+                                                    reinterpret_cast<const double2 *>(bd), n2,
+                                                    ad + 2 * n2, bd + 2 * n2, static_cast<int>(n - 2 * n2),
+                                                    partials);
+        } else {
+            grid = vec_grid(n);
+            k_dot<double, double><<<grid, kDotThreads, 0, s>>>(ad, bd, n, partials);
+        }
+    } else if (ak == kF32 && bk == kF32) {
+        const float *af = static_cast<const float *>(a), *bf = static_cast<const float *>(b);
+        if (aligned16(a) && aligned16(b)) {
+            const int64_t n4 = n / 4;
+            grid = vec_grid(n4);
+            k_dot_f32v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<const float4 *>(af),
+                                                    reinterpret_cast<const float4 *>(bf), n4,
+                                                    af + 4 * n4, bf + 4 * n4, static_cast<int>(n - 4 * n4),
+                                                    partials);
+        } else {
+            grid = vec_grid(n);
+            k_dot<float, float><<<grid, kDotThreads, 0, s>>>(af, bf, n, partials);
+        }
+    } else {
         return cudaErrorInvalidValue;
+    }
     k_reduce<<<1, kDotThreads, 0, s>>>(partials, grid, sc, op, dst);
     return cudaGetLastError();
 }
 
 cudaError_t cg_update32(float *d, float *r, const float *p, const float *q, int64_t n,
                         double *partials, double *sc, cudaStream_t s) {
-    const int grid = vec_grid(n);
-    k_update32<<<grid, kDotThreads, 0, s>>>(d, r, p, q, sc, n, partials);
+    int grid;
+    if (aligned16(d) && aligned16(r) && aligned16(p) && aligned16(q)) {
+        const int64_t n4 = n / 4;
+        grid = vec_grid(n4);
+        k_update32v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<float4 *>(d), reinterpret_cast<float4 *>(r),
+                                                 reinterpret_cast<const float4 *>(p),
+                                                 reinterpret_cast<const float4 *>(q), sc, n4, d + 4 * n4,
+                                                 r + 4 * n4, p + 4 * n4, q + 4 * n4,
+                                                 static_cast<int>(n - 4 * n4), partials);
+    } else {
+        grid = vec_grid(n);
+        k_update32<<<grid, kDotThreads, 0, s>>>(d, r, p, q, sc, n, partials);
+    }
     k_reduce<<<1, kDotThreads, 0, s>>>(partials, grid, sc, kOpBeta, 0);
     return cudaGetLastError();
 }
@@ -174,7 +310,15 @@ cudaError_t cg_update64(double *x, double *r, const double *p, const double *q, 
 
 cudaError_t cg_direction(void *p, const void *r, int k, const double *sc, int64_t n, cudaStream_t s) {
     const int grid = vec_grid(n);
-    if (k == kF32)
+    if (k == kF32 && aligned16(p) && aligned16(r)) {
+        const int64_t n4 = n / 4;
+        float *pf = static_cast<float *>(p);
+        const float *rf = static_cast<const float *>(r);
+        k_direction32v<<<vec_grid(n4), kDotThreads, 0, s>>>(reinterpret_cast<float4 *>(pf),
+                                                            reinterpret_cast<const float4 *>(rf), sc, n4,
+                                                            pf + 4 * n4, rf + 4 * n4,
+                                                            static_cast<int>(n - 4 * n4));
+    } else if (k == kF32)
         k_direction<float><<<grid, kDotThreads, 0, s>>>(static_cast<float *>(p), static_cast<const float *>(r), sc, n);
     else
         k_direction<double><<<grid, kDotThreads, 0, s>>>(static_cast<double *>(p), static_cast<const double *>(r), sc, n);

@@ -52,13 +52,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, u
         : "memory");
 }
 
+// The suspend-time hint (ns) lets the hardware park the waiting warp until the
+// phase completes instead of returning at once, so waiting warps do not take
+// issue slots from the warps that compute.
+constexpr uint32_t kTryWaitSuspendNs = 20000;
+
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(kTryWaitSuspendNs) : "memory");
     return ok;
 }
 
@@ -90,16 +95,22 @@ __device__ __forceinline__ void set_error(int32_t *err, int32_t code) {
 
 // ---------------------------------------------------------------------------
 // FP32 -> FP64 widening without the FP64 pipe.  On GB300 the F2F.F64.F32
-// conversion issues on the (narrow) FP64 unit, at the DFMA rate; normal numbers
-// and zeros are widened here with integer operations instead (exact: the
-// exponent is rebiased by 1023-127 and the 23-bit mantissa moved up 29 bits).
-// Subnormals, infinities and NaNs fall back to the hardware conversion.
+// conversion issues on the (narrow) FP64 unit, at the DFMA rate; here every
+// input is widened with FP32/integer operations and no branch (a conditional
+// hardware fallback would be if-converted and issued for every element):
+//   normal:    exponent rebiased by 1023-127, 23-bit mantissa moved up 29 bits;
+//   zero:      sign only;
+//   inf/NaN:   exponent field 0x7ff, payload moved up 29 bits;
+//   subnormal: scaled by 2^24 in FP32 (exact, the result is normal), widened as
+//              a normal number, and the 24 taken off the FP64 exponent field.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double widen(float f) {
-    const uint32_t u = __float_as_uint(f);
+    const uint32_t a0 = __float_as_uint(f) & 0x7fffffffu;
+    const bool sub = (a0 != 0u) && (a0 < 0x00800000u);
+    const uint32_t u = __float_as_uint(sub ? f * 16777216.0f : f);
     const uint32_t a = u & 0x7fffffffu;
-    if (a != 0u && (a - 0x00800000u) >= 0x7f000000u) return static_cast<double>(f);
-    const uint32_t hi = (u & 0x80000000u) | (a ? ((a >> 3) + 0x38000000u) : 0u);
+    const uint32_t bias = (a >= 0x7f800000u) ? 0x70000000u : (sub ? 0x38000000u - (24u << 20) : 0x38000000u);
+    const uint32_t hi = (u & 0x80000000u) | (a ? (a >> 3) + bias : 0u);
     const uint32_t lo = u << 29;
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
@@ -124,21 +135,22 @@ struct AccF64 {
     __device__ __forceinline__ double get() const { return s; }
 };
 
-// Float-float accumulation on the FP32 pipe for FP32-stored operands: the product
-// of two floats is split exactly into hi + lo (FMA residual), and the running sum
-// is a normalised pair (hi, lo) updated by Knuth's two-sum.  Relative accuracy is
-// about 2^-44 of sum |a_ij x_j|, far inside the FP32-storage tolerance, while
-// using no FP64 instructions per entry.
+// Float-float accumulation on the FP32 pipe for FP32-stored operands (the Dot2
+// scheme of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005): each
+// product of two floats is split exactly into ph + pl (FMA residual), ph is
+// added to the running sum h by Knuth's two-sum, and the rounding error of that
+// addition plus pl is collected in l.  The value is h + l; its error is about
+// n^2 2^-48 sum |a_ij x_j| for n terms, far inside the FP32-storage tolerance,
+// while using no FP64 instructions per entry.
 struct AccFF {
     float h, l;
     __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }
     __device__ __forceinline__ void add_pair(float ph, float pl) {
         const float s = h + ph;
         const float bb = s - h;
-        float e = (h - (s - bb)) + (ph - bb);
-        e += l + pl;
-        h = s + e;
-        l = e - (h - s);
+        const float e = (h - (s - bb)) + (ph - bb);
+        h = s;
+        l = l + (e + pl);
     }
     __device__ __forceinline__ void fma(float v, float x) {
         const float ph = v * x;

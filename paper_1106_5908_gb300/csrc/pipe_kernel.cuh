@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
             chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
             for (int q = lane; q < r1 - r0; q += 32)
-                store_row(y, r0 + q, srow[q].get(), alpha, beta, plain, m.rmap);
+                store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
         }
         // every lane is done with stage s (and the row buffer) before lane 0
         // refills it at the next iteration
@@ -370,7 +370,7 @@ k_pipe3(const WarpParams p) {
             chunk_lane<E, VT, XT, ACC>(vals, xcur, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
             for (int q = lane; q < r1 - r0; q += 32)
-                store_row(y, r0 + q, srow[q].get(), alpha, beta, plain, m.rmap);
+                store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
         }
         __syncwarp();  // stage s and the row buffer are free again
 #pragma unroll

@@ -84,6 +84,22 @@ __device__ __forceinline__ void store_row(YT *__restrict__ y, int64_t row, doubl
     y[row] = narrow<YT>(out);
 }
 
+// Store a finished row sum.  A float-float sum bound for an FP32 y with
+// alpha = 1, beta = 0 is rounded to float directly (h + l on the FP32 pipe);
+// every other case goes through FP64.
+template <typename YT, typename ACC>
+__device__ __forceinline__ void store_acc(YT *__restrict__ y, int64_t row, const ACC &a, double alpha,
+                                          double beta, bool plain, const int32_t *rmap) {
+    if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
+        if (plain) {
+            if (rmap) row = __ldg(rmap + row);
+            y[row] = a.h + a.l;
+            return;
+        }
+    }
+    store_row(y, row, a.get(), alpha, beta, plain, rmap);
+}
+
 __device__ __forceinline__ AccF64 shfl_up_acc(const AccF64 &a, int d) {
     AccF64 b;
     b.s = __shfl_up_sync(0xffffffffu, a.s, d);
@@ -123,7 +139,7 @@ __device__ __forceinline__ void long_row(const MatRef &m, const ChunkDesc &d, co
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
-    if (lane == 0) store_row(y, d.r0, acc.get(), alpha, beta, plain, m.rmap);
+    if (lane == 0) store_acc(y, d.r0, acc, alpha, beta, plain, m.rmap);
 }
 
 // A chunk with empty rows: one row per lane straight from global memory.
@@ -142,7 +158,7 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
             else
                 acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
         }
-        store_row(y, r, acc.get(), alpha, beta, plain, m.rmap);
+        store_acc(y, r, acc, alpha, beta, plain, m.rmap);
     }
 }
 
@@ -281,7 +297,7 @@ __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
     ACC *srow = s_rows[wib];
     chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
     __syncwarp();
-    for (int i = lane; i < r1 - r0; i += 32) store_row(y, r0 + i, srow[i].get(), alpha, beta, plain, m.rmap);
+    for (int i = lane; i < r1 - r0; i += 32) store_acc(y, r0 + i, srow[i], alpha, beta, plain, m.rmap);
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>

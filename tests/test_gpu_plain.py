@@ -186,7 +186,8 @@ def test_laplace3d_160_fp32(c3):
 
 def test_autotuner_choices():
     """The tuner picks the three-stage chunk kernel for scattered columns and the
-    two-stage one for stencils, with entries per lane from the mean row length."""
+    two-stage one for stencils, with entries per lane from the mean row length
+    (FP64), or from the column scatter (FP32 storage)."""
     from paper_1106_5908_gb300 import Matrix
     H = W.hamiltonian_like(50000, seed=3)
     info = Matrix.from_csr(H.row_ptr, H.col_idx, H.val, H.n_cols).info()
@@ -197,3 +198,34 @@ def test_autotuner_choices():
     S27 = W.stencil27(20, seed=1)
     info = Matrix.from_csr(S27.row_ptr, S27.col_idx, S27.val, S27.n_cols).info()
     assert (info["family"], info["E"]) == (0, 15)
+    # FP32 storage: 15 entries per lane unless the columns are scattered
+    for A, want in ((H, (0, 7)), (L3, (0, 15)), (S27, (0, 15))):
+        info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
+        assert (info["family"], info["E"]) == want
+
+
+@pytest.mark.parametrize("acc", ["ff", "f64"])
+@pytest.mark.parametrize("plan", [(0, 7), (0, 15), (0, 16), (1, 1)])
+def test_fp32_widening_exact(acc, plan):
+    """FP32 inputs are widened to FP64 exactly, across every class of float: with
+    a unit diagonal, y_i = x_i as a double (zeros, subnormals, the normal range
+    ends, and for FP64 accumulation also infinities and NaN)."""
+    rng = np.random.default_rng(5)
+    bits = np.concatenate([
+        np.array([0x00000000, 0x80000000, 0x00000001, 0x80000001, 0x007fffff, 0x807fffff, 0x00400000,
+                  0x00800000, 0x80800000, 0x7f7fffff, 0xff7fffff, 0x3f800000, 0x33800000], np.uint32),
+        rng.integers(1, 0x00800000, 64, dtype=np.uint32),                     # subnormals
+        rng.integers(0x00800000, 0x7f800000, 256, dtype=np.uint32) | (rng.integers(0, 2, 256, dtype=np.uint32) << 31)])
+    if acc == "f64":
+        bits = np.concatenate([bits, np.array([0x7f800000, 0xff800000, 0x7fc00000, 0x7fa00001], np.uint32)])
+    x32 = bits.view(np.float32)
+    n = x32.size
+    A = W.CRS(np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n, np.float32), n)
+    M = make(A)
+    M.set_accumulator(acc)
+    M.set_plan(*plan)
+    y = host(M.apply(dev(x32), out_dtype=torch.float64))
+    want = x32.astype(np.float64)
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(y), nan)
+    assert np.array_equal(y[~nan], want[~nan]), np.flatnonzero(y[~nan] != want[~nan])[:8]
