@@ -100,6 +100,54 @@ __device__ __forceinline__ void store_acc(YT *__restrict__ y, int64_t row, const
     store_row(y, row, a.get(), alpha, beta, plain, rmap);
 }
 
+// Row epilogue of a regular chunk (at most kWarpRowCap rows, lane l owns rows
+// l, l+32, l+64): the output index of each row (through rmap) and, when beta is
+// nonzero, its old y value are loaded before the FMA chains run, so that their
+// latency overlaps the chains instead of following them.
+template <typename YT>
+struct RowEpilogue {
+    static constexpr int K = kWarpRowCap / 32;
+    int64_t dst[K];
+    double old[K];
+    __device__ __forceinline__ void prefetch(const YT *__restrict__ y, const int32_t *__restrict__ rmap, int r0,
+                                             int nrows, bool need_old, int lane) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int q = lane + 32 * k;
+            dst[k] = r0 + q;
+            if (rmap && q < nrows) dst[k] = __ldg(rmap + r0 + q);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int q = lane + 32 * k;
+            old[k] = 0.0;
+            if (need_old && q < nrows) old[k] = widen(y[dst[k]]);
+        }
+    }
+    template <typename ACC>
+    __device__ __forceinline__ void store(YT *__restrict__ y, const ACC *srow, int nrows, double alpha,
+                                          double beta, bool plain, int lane) const {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int q = lane + 32 * k;
+            if (q >= nrows) break;
+            const ACC a = srow[q];
+            if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
+                if (plain) {
+                    y[dst[k]] = a.h + a.l;
+                    continue;
+                }
+            }
+            const double v = a.get();
+            double out;
+            if (plain) out = v;
+            else if (beta == 0.0) out = alpha * v;
+            else out = fma(alpha, v, beta * old[k]);
+            y[dst[k]] = narrow<YT>(out);
+        }
+    }
+};
+
 __device__ __forceinline__ AccF64 shfl_up_acc(const AccF64 &a, int d) {
     AccF64 b;
     b.s = __shfl_up_sync(0xffffffffu, a.s, d);
