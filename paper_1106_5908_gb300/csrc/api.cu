@@ -952,13 +952,19 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
         spmv_split_destroy(sp);
         return st;
     }
-    // the split parts use the tile kernel with the parent's per-thread work
-    // the split parts use the tuned chunk kernels; the nonlocal columns index the
-    // halo, not rows, so gather one chunk ahead there
-    if (sp->Anl->vk == kF64) {
-        sp->Anl->family = 3;
-        sp->Anl->E = 15;
+    // Plans of the parts (measured on the Hamiltonian-like matrix, 8 blocks): the
+    // local part keeps mostly near columns, whose gathers hit L1, so it runs on
+    // the two-stage kernel (294 vs 311 us for the whole split product); the
+    // nonlocal part's gathers go to the halo buffer, so it gathers one chunk
+    // ahead with 15 entries per lane (three-stage kernel, row epilogue loaded
+    // ahead).
+    if (sp->Aloc->family == 3) {
+        const double mean = n ? static_cast<double>(sp->Aloc->nnz) / n : 0.0;
+        sp->Aloc->family = 0;
+        sp->Aloc->E = (mean < 20.0) ? 7 : 15;
     }
+    sp->Anl->family = 3;
+    sp->Anl->E = 15;
     if (halo_count_out)
         for (int b = 0; b < nblocks; ++b) halo_count_out[b] = sp->halo_count[b];
     *out = sp;
