@@ -320,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
 
     forms = {}
     if rank == 0 and not args.no_forms:
-        forms = measure_forms(M64, A, x, dev, form_ms, b_plain)
+        forms = measure_forms(M64, A, x, dev, form_ms, b_plain, SP)
     if rank != 0:
         return
     peaks = measured_peaks()
@@ -406,14 +406,38 @@ def _time(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_forms(M64, A, x, dev, form_ms, b_plain):
-    """The other forms, each against the plain FP64 product on the same GPU:
-    block vectors on the same matrix; mixed-precision IR-CG against FP64 CG on the
-    160^3 7-point Poisson matrix; the reverse pass on the 128^3 27-point pattern;
-    256 uneven matrices in one persistent graph launch."""
+def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
+    """The other forms, each against the plain FP64 product on the same GPU: the
+    three schedules of the split product (Fig. kernel_schemes) on nonzero-balanced
+    and equal-rows blocks; block vectors on the same matrix; mixed-precision IR-CG
+    against FP64 CG on the 160^3 7-point Poisson matrix; the reverse pass on the
+    128^3 27-point pattern; 256 uneven matrices in one persistent graph launch."""
     import torch
     from paper_1106_5908_gb300 import Batch, Matrix, cg, ir_cg
     out = {}
+    try:  # split schedules: vector mode, naive overlap (one stream), task mode (two streams)
+        xd = torch.as_tensor(x).to(dev)
+        ys = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        sched = {}
+        for label, sp in (("equal_nnz", SP), ("equal_rows", M64.split(8, equal_rows=True))):
+            h = int(sp.plan()["total_halo"])
+            bv = model.bytes_split_vector(A.n_rows, A.n_cols, A.nnz, h)
+            bs = model.bytes_split(A.n_rows, A.n_cols, A.nnz, h)
+            with torch.cuda.stream(s1):
+                t_vec = _time(lambda: sp.apply_vector(xd, ys, stream=s1), 10)
+                t_naive = _time(lambda: sp.apply(xd, ys, s_compute=s1, s_comm=s1), 10)
+                t_task = _time(lambda: sp.apply(xd, ys, s_compute=s1, s_comm=s2), 10)
+            sched[label] = {
+                "total_halo": h,
+                "vector_mode": {"ms": t_vec, "GBs": bv / t_vec / 1e6, "time_vs_plain": t_vec / form_ms["plain"]},
+                "naive_overlap": {"ms": t_naive, "GBs": bs / t_naive / 1e6,
+                                  "time_vs_plain": t_naive / form_ms["plain"]},
+                "task_mode": {"ms": t_task, "GBs": bs / t_task / 1e6, "time_vs_plain": t_task / form_ms["plain"]}}
+        out["split_schedules"] = sched
+        del xd, ys
+    except Exception as e:  # reported, not hidden
+        out["split_schedules"] = {"error": repr(e)}
     for nrhs in (4, 8, 16, 32):
         X = torch.rand(A.n_rows, nrhs, dtype=torch.float64, device=dev) * 2 - 1
         Y = torch.empty_like(X)

@@ -137,7 +137,10 @@ spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt
  * (sorted distinct nonlocal columns), the local part A_loc and the nonlocal part
  * A_nl with columns renumbered into the concatenated halo buffer.
  * halo_count_out (optional HOST array of nblocks) receives the halo sizes.
- * The split handle references h, which must outlive it. */
+ * The split handle references h, which must outlive it; its parts hold copies
+ * of h's values taken at creation (after spmv_set_values on h, create the split
+ * again).  Equal-rows blocks (the "constant rows" case of Fig. 6) are
+ * block_row_start[b] = floor(b*n_rows/nblocks). */
 spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nblocks,
                               const int32_t *block_row_start, int32_t *halo_count_out);
 void spmv_split_destroy(spmv_split_handle hs);
@@ -160,7 +163,18 @@ spmv_status spmv_split_get_plan(spmv_split_handle hs, int32_t *nblocks, int32_t 
 spmv_status spmv_apply_split(spmv_split_handle hs, double alpha, const double *x, double beta,
                              double *y, void *s_compute, void *s_comm);
 
-/* Copy the halo buffer filled by the last spmv_apply_split to a HOST array of
+/* Split spMVM in vector mode (Sect. 3.4, Fig. kernel_schemes (a): the halo
+ * exchange completes before any computation): on stream s, gather the whole
+ * halo, then one pass over the full matrix, whose nonlocal columns are
+ * renumbered into the extended vector [x | halo] at split creation, computes
+ * y = alpha*A*x + beta*y, writing y once (Eq. 1 traffic plus the gather).  The
+ * plan holds a handle-owned copy of the extended vector and of the renumbered
+ * matrix.  FP64 x and y only; x and y are borrowed device pointers.
+ * SPMV_ERR_UNSUPPORTED if n_rows + total halo does not fit in int32. */
+spmv_status spmv_apply_split_vector(spmv_split_handle hs, double alpha, const double *x, double beta,
+                                    double *y, void *stream);
+
+/* Copy the halo buffer filled by the last spmv_apply_split (task mode) to a HOST array of
  * total-halo doubles (synchronises s). */
 spmv_status spmv_split_get_halo(spmv_split_handle hs, double *halo_out, void *stream);
 

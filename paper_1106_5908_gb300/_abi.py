@@ -30,7 +30,8 @@ SPMV_NOALLOC_MAX_COLS = 1 << 20
 EXPORTS = (
     "spmv_status_string", "spmv_version", "spmv_create", "spmv_destroy", "spmv_set_values",
     "spmv_get_info", "spmv_row_histogram", "spmv_set_plan", "spmv_set_accumulator", "spmv_apply", "spmv_split_create",
-    "spmv_split_destroy", "spmv_split_get_plan", "spmv_apply_split", "spmv_split_get_halo",
+    "spmv_split_destroy", "spmv_split_get_plan", "spmv_apply_split", "spmv_apply_split_vector",
+    "spmv_split_get_halo",
     "spmm_apply", "spmv_backward", "spmv_get_transpose", "spmv_transpose_noalloc", "spmv_batched_create",
     "spmv_batched_destroy", "spmv_batched_apply", "spmv_batched_get_info", "spmv_ir_cg",
     "spmv_cg", "spmv_check_device_error",
@@ -77,6 +78,7 @@ def load() -> ctypes.CDLL:
         "spmv_split_destroy": (None, [vp]),
         "spmv_split_get_plan": (st, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "spmv_apply_split": (st, [vp, f64, vp, f64, vp, vp, vp]),
+        "spmv_apply_split_vector": (st, [vp, f64, vp, f64, vp, vp]),
         "spmv_split_get_halo": (st, [vp, vp, vp]),
         "spmm_apply": (st, [vp, i32, f64, vp, f64, vp, st, vp]),
         "spmv_backward": (st, [vp, f64, vp, vp, vp, vp, vp]),
@@ -130,6 +132,7 @@ spmv_apply = _fwd("spmv_apply")
 spmv_split_create = _fwd("spmv_split_create")
 spmv_split_destroy = _fwd("spmv_split_destroy")
 spmv_split_get_plan = _fwd("spmv_split_get_plan")
+spmv_apply_split_vector = _fwd("spmv_apply_split_vector")
 spmv_apply_split = _fwd("spmv_apply_split")
 spmv_split_get_halo = _fwd("spmv_split_get_halo")
 spmm_apply = _fwd("spmm_apply")

@@ -233,6 +233,10 @@ struct spmv_split {
     double *d_halo = nullptr;
     spmv_handle Aloc = nullptr, Anl = nullptr;
     cudaEvent_t ev_x = nullptr, ev_halo = nullptr;
+    // vector mode: the whole matrix with each nonlocal column renumbered to
+    // n + (its position in the concatenated halo), applied to xe = [x | halo]
+    spmv_handle Avec = nullptr;
+    double *d_xe = nullptr;
 };
 
 struct spmv_batch {
@@ -871,6 +875,7 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
     std::vector<int32_t> rp_loc(static_cast<size_t>(n) + 1, 0), rp_nl(static_cast<size_t>(n) + 1, 0);
     std::vector<int32_t> col_loc, col_nl;
     std::vector<double> val_loc, val_nl;
+    std::vector<int32_t> col_vec(static_cast<size_t>(nnz));
     col_loc.reserve(static_cast<size_t>(nnz));
     val_loc.reserve(static_cast<size_t>(nnz));
     for (int b = 0; b < nblocks; ++b) {
@@ -899,9 +904,11 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
                 if (c >= lo && c < hi) {
                     col_loc.push_back(c);
                     val_loc.push_back(val[k]);
+                    col_vec[k] = c;
                 } else {
                     col_nl.push_back(pos[c]);
                     val_nl.push_back(val[k]);
+                    col_vec[k] = n + pos[c];
                 }
             }
             rp_loc[i + 1] = static_cast<int32_t>(col_loc.size());
@@ -910,7 +917,7 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
         sp->nnz_local[b] = rp_loc[hi] - rp_loc[lo];
         sp->nnz_nonlocal[b] = rp_nl[hi] - rp_nl[lo];
     }
-    if (sp->total_halo >= (int64_t(1) << 31)) {
+    if (sp->total_halo + n >= (int64_t(1) << 31)) {
         delete sp;
         return SPMV_ERR_UNSUPPORTED;
     }
@@ -945,6 +952,12 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
         cudaMemcpy(sp->d_halo_map, sp->h_halo_map.data(), static_cast<size_t>(sp->total_halo) * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess)
         st = SPMV_ERR_CUDA;
+    if (st == SPMV_OK)
+        st = create_from_host(&sp->Avec, n, static_cast<int32_t>(n + sp->total_halo), nnz,
+                              std::vector<int32_t>(h->h_rp), col_vec.data(), val.data(), kF64, kF64, false, s,
+                              col_vec.data());
+    if (st == SPMV_OK && dmalloc(&sp->d_xe, static_cast<size_t>(n + sp->total_halo)) != cudaSuccess)
+        st = SPMV_ERR_ALLOC;
     if (st == SPMV_OK && (cudaEventCreateWithFlags(&sp->ev_x, cudaEventDisableTiming) != cudaSuccess ||
                           cudaEventCreateWithFlags(&sp->ev_halo, cudaEventDisableTiming) != cudaSuccess))
         st = SPMV_ERR_CUDA;
@@ -977,6 +990,8 @@ void spmv_split_destroy(spmv_split_handle hs) {
     cudaDeviceSynchronize();
     destroy_matrix(hs->Aloc);
     destroy_matrix(hs->Anl);
+    destroy_matrix(hs->Avec);
+    cudaFree(hs->d_xe);
     cudaFree(hs->d_halo_map);
     cudaFree(hs->d_halo);
     if (hs->ev_x) cudaEventDestroy(hs->ev_x);
@@ -1019,6 +1034,23 @@ spmv_status spmv_apply_split(spmv_split_handle hs, double alpha, const double *x
     if (sm != sc) CK(cudaStreamWaitEvent(sc, hs->ev_halo, 0));
     if (hs->Anl->nnz > 0) st = apply_impl(hs->Anl, alpha, hs->d_halo, kF64, 1.0, y, kF64, sc);
     return st;
+}
+
+// Vector mode (Sect. 3.4, Fig. kernel_schemes (a)): the whole halo is gathered
+// first, then one pass over the full matrix reads local columns from x and
+// nonlocal ones from the halo (both in xe), writing y once.
+spmv_status spmv_apply_split_vector(spmv_split_handle hs, double alpha, const double *x, double beta,
+                                    double *y, void *stream) {
+    if (!hs) return SPMV_ERR_INVALID_ARG;
+    spmv_matrix *A = hs->A;
+    if (A->n_rows > 0 && (!x || !y)) return SPMV_ERR_INVALID_ARG;
+    if (!hs->Avec) return SPMV_ERR_UNSUPPORTED;
+    DeviceGuard g(A->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = A->n_rows;
+    if (n > 0) CK(cudaMemcpyAsync(hs->d_xe, x, static_cast<size_t>(n) * 8, cudaMemcpyDeviceToDevice, s));
+    CK(launch_gather(x, hs->d_halo_map, hs->d_xe + n, hs->total_halo, s));
+    return apply_impl(hs->Avec, alpha, hs->d_xe, kF64, beta, y, kF64, s);
 }
 
 spmv_status spmv_split_get_halo(spmv_split_handle hs, double *halo_out, void *stream) {

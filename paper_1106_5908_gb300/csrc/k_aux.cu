@@ -94,12 +94,28 @@ cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk
 // Halo gather (the stand-in for the MPI exchange of Sect. 3.1-3.5): every
 // nonlocal column a block needs is copied into the contiguous halo buffer.
 // ---------------------------------------------------------------------------
+// halo[h] = x[map[h]]: each thread takes four entries a blockDim apart per
+// step, so four map loads and then four x gathers are in flight at once.
 __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ x,
                                                 const int32_t *__restrict__ map,
                                                 double *__restrict__ halo, int64_t n) {
-    for (int64_t h = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; h < n;
-         h += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        halo[h] = __ldg(x + __ldg(map + h));
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * 4;
+    for (int64_t h0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * 4 + threadIdx.x; h0 < n; h0 += step) {
+        int32_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t h = h0 + static_cast<int64_t>(u) * blockDim.x;
+            c[u] = (h < n) ? __ldg(map + h) : -1;
+        }
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (c[u] >= 0) ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t h = h0 + static_cast<int64_t>(u) * blockDim.x;
+            if (h < n) halo[h] = v[u];
+        }
+    }
 }
 
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
@@ -108,7 +124,7 @@ cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t want = (n + 255) / 256;
+    int64_t want = (n + 1023) / 1024;
     int grid = static_cast<int>(want < 8LL * sms ? want : 8LL * sms);
     k_gather<<<grid, 256, 0, s>>>(x, map, halo, n);
     return cudaGetLastError();

@@ -68,6 +68,14 @@ def bytes_plain(n_rows: int, n_cols: int, nnz: int, val_bytes: int = 8, x_bytes:
     return int(b)
 
 
+def bytes_split_vector(n_rows: int, n_cols: int, nnz: int, total_halo: int,
+                       beta_nonzero: bool = False) -> int:
+    """Vector mode: plain FP64 bytes, plus x copied into the extended vector
+    (read + write) and the halo traffic (map read, gathered x read, halo write,
+    halo read: 4 + 8 + 8 + 8 bytes per halo entry); y is written once."""
+    return int(bytes_plain(n_rows, n_cols, nnz, beta_nonzero=beta_nonzero) + 16 * n_rows + 28 * total_halo)
+
+
 def bytes_split(n_rows: int, n_cols: int, nnz: int, total_halo: int,
                 beta_nonzero: bool = False) -> int:
     """Plain FP64 bytes plus the second pass over y (read + write, Eq. 2) and the

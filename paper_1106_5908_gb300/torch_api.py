@@ -169,7 +169,13 @@ class Matrix:
                   "spmv_get_transpose")
         return rp, ci[: self.nnz], pm[: self.nnz]
 
-    def split(self, nblocks: int = 8, block_row_start: Optional[Sequence[int]] = None) -> "Split":
+    def split(self, nblocks: int = 8, block_row_start: Optional[Sequence[int]] = None,
+              equal_rows: bool = False) -> "Split":
+        """Local/nonlocal split over ``nblocks`` contiguous row blocks: balanced
+        nonzeros by default, ``equal_rows`` for blocks of floor(b*n/nblocks)
+        rows (Fig. 6's constant-rows case), or explicit ``block_row_start``."""
+        if equal_rows and block_row_start is None:
+            block_row_start = [b * self.n_rows // nblocks for b in range(nblocks + 1)]
         return Split(self, nblocks, block_row_start)
 
 
@@ -225,6 +231,15 @@ class Split:
         sm = _stream(s_comm) if s_comm is not None else sc
         abi.check(abi.spmv_apply_split(self._h, float(alpha), _dptr(x), float(beta), _dptr(y), sc, sm),
                   "spmv_apply_split")
+        return y
+
+    def apply_vector(self, x: torch.Tensor, y: Optional[torch.Tensor] = None, alpha: float = 1.0,
+                     beta: float = 0.0, stream=None) -> torch.Tensor:
+        """Vector mode: gather the whole halo, then one pass over the full matrix."""
+        if y is None:
+            y = torch.empty(self.A.n_rows, dtype=torch.float64, device=x.device)
+        abi.check(abi.spmv_apply_split_vector(self._h, float(alpha), _dptr(x), float(beta), _dptr(y),
+                                              _stream(stream)), "spmv_apply_split_vector")
         return y
 
     def halo(self, stream=None) -> np.ndarray:

@@ -1,7 +1,7 @@
 """GPU parity on the Hamiltonian-like matrix at full size (N = 4,194,304): plain
-FP64, the local/nonlocal split over 8 nonzero-balanced blocks (plan and halo
-bit-exact, result within tolerance, on one and on two streams), FP32 storage, and
-block vectors."""
+FP64, the local/nonlocal split over 8 nonzero-balanced or equal-rows blocks (plan
+and halo bit-exact, result within tolerance, in task mode on two streams, naive
+overlap on one stream, and vector mode), FP32 storage, and block vectors."""
 import numpy as np
 import pytest
 
@@ -82,6 +82,52 @@ def test_c2_split(c2, m2):
     sp.apply(xd, y, 0.5, -1.0, s_compute=s1, s_comm=s2)
     s1.synchronize()
     assert_within(host(y), ref2, bound2, 1e-13, "split alpha/beta")
+
+
+@pytest.mark.parametrize("equal_rows", [False, True])
+def test_c2_split_vector_mode(c2, m2, equal_rows):
+    """Vector mode (Fig. kernel_schemes (a)) gives the plain product; equal-rows
+    blocks start at floor(b*n/8)."""
+    A, x, ref, bound = c2
+    sp = m2.split(8, equal_rows=equal_rows)
+    plan = sp.plan()
+    if equal_rows:
+        assert_bitexact(plan["block_start"], np.array([b * A.n_rows // 8 for b in range(9)]), "equal rows")
+    cnt, hmap, _, _ = oracle.split_halo(A.row_ptr, A.col_idx, A.n_cols, plan["block_start"])
+    assert_bitexact(plan["halo_map"], hmap, "halo map")
+    xd = dev(x)
+    assert_within(host(sp.apply_vector(xd)), ref, bound, 1e-13, "vector mode")
+    assert_within(host(sp.apply(xd, s_comm=torch.cuda.Stream())), ref, bound, 1e-13, "task mode")
+    torch.cuda.synchronize()
+    y0 = W.uniform(A.n_rows, 6)
+    ref2, bound2 = oracle.spmv(*A.astuple(), x, -1.5, 0.25, y0, with_bound=True)
+    y = dev(y0)
+    sp.apply_vector(xd, y, -1.5, 0.25)
+    assert_within(host(y), ref2, bound2, 1e-13, "vector mode alpha/beta")
+
+
+def test_split_vector_mode_small_and_integer():
+    """Vector mode on explicit blocks (one empty), one block (no halo) and
+    integer data (bit-exact)."""
+    from paper_1106_5908_gb300 import Matrix
+    A = W.hamiltonian_like(5000, seed=4)
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+    x = W.uniform(5000, 1)
+    ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
+    for starts in ([0, 100, 100, 2500, 4999, 5000], [0, 5000]):
+        sp = M.split(len(starts) - 1, starts)
+        assert_within(host(sp.apply_vector(dev(x))), ref, bound, 1e-13, f"vector mode {starts}")
+    assert M.split(1).plan()["total_halo"] == 0
+    Ai = W.random_csr(3000, 3000, seed=8, integer=True, max_len=30)
+    Mi = Matrix.from_csr(Ai.row_ptr, Ai.col_idx, Ai.val, Ai.n_cols)
+    xi = W.integers(3000, 9).astype(np.float64)
+    refi = oracle.spmv(*Ai.astuple(), xi)
+    for eq in (False, True):
+        spi = Mi.split(8, equal_rows=eq)
+        assert_bitexact(host(spi.apply_vector(dev(xi))), refi, f"vector mode integer eq={eq}")
+        y = spi.apply(dev(xi), s_comm=torch.cuda.Stream())
+        torch.cuda.synchronize()
+        assert_bitexact(host(y), refi, f"task mode integer eq={eq}")
 
 
 def test_split_explicit_blocks_small():
