@@ -479,11 +479,18 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
         M5.backward(g5, x5)
         ms_b = _time(lambda: M5.backward(g5, x5), 10)
         ms_gx = _time(lambda: M5.backward(g5, x5, need_val=False), 10)
+        # after new values the transposed values are laid out again (one
+        # permutation pass): time set_values + backward minus set_values alone
+        v5 = torch.as_tensor(A5.val).to(dev)
+        ms_sv = _time(lambda: M5.set_values(v5), 10)
+        ms_svb = _time(lambda: (M5.set_values(v5), M5.backward(g5, x5)), 10)
         out["backward_27pt128"] = {
             "forward_ms": ms_f, "backward_ms": ms_b, "grad_x_ms": ms_gx,
+            "backward_after_new_values_ms": ms_svb - ms_sv,
             "forward_GBs": model.bytes_plain(A5.n_rows, A5.n_cols, A5.nnz) / ms_f / 1e6,
             "backward_GBs": model.bytes_backward(A5.n_rows, A5.n_cols, A5.nnz) / ms_b / 1e6,
             "time_vs_plain": ms_b / ms_f}
+        del v5
         del M5, x5, g5, y5
     except Exception as e:
         out["backward_27pt128"] = {"error": repr(e)}

@@ -215,6 +215,12 @@ struct spmv_matrix {
     // transposed structure (built on first use)
     bool has_T = false;
     int32_t *d_rowT = nullptr, *d_colT = nullptr, *d_perm = nullptr;
+    // values of A^T in its row order (val[perm]): laid out by the second reverse
+    // pass on the same values (valT_requested records the first one) and
+    // invalidated by spmv_set_values
+    void *d_valT = nullptr;
+    bool valT_valid = false;
+    bool valT_requested = false;
     std::vector<int32_t> h_rowT;
     std::map<std::pair<int, int>, TileTable> tablesT;
     // FP32 mirror for IR-CG
@@ -438,6 +444,7 @@ void destroy_matrix(spmv_matrix *h) {
     cudaFree(h->d_rowT);
     cudaFree(h->d_colT);
     cudaFree(h->d_perm);
+    cudaFree(h->d_valT);
     free_tables(h->tables);
     free_tables(h->tablesT);
     free_chunk_map(h->chunks);
@@ -726,6 +733,8 @@ spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *
     if (h->nnz == 0) return SPMV_OK;
     CK(launch_convert(val, t, h->d_val, h->vk, h->nnz, s));
     if (h->mirror32) CK(launch_convert(val, t, h->mirror32->d_val, kF32, h->nnz, s));
+    h->valT_valid = false;
+    h->valT_requested = false;
     return SPMV_OK;
 }
 
@@ -1113,18 +1122,33 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
     if (grad_x && h->n_cols > 0) {
         spmv_status st = ensure_transpose(h, s);
         if (st != SPMV_OK) return st;
-        // grad_x = alpha * A^T g: warp chunks over the rows of A^T, values read
-        // through the permutation
+        // grad_x = alpha * A^T g: warp chunks over the rows of A^T.  The first
+        // reverse pass on a set of values reads them through the permutation
+        // (val[perm], inside the kernel); a second one on the same values lays
+        // them out in the order of A^T once (a streaming permutation pass), and
+        // from then on the product streams them like a forward product.
+        const size_t vb = (h->vk == kF64) ? 8 : 4;
+        if (!h->valT_valid && h->valT_requested && h->nnz > 0) {
+            if (!h->d_valT && cudaMalloc(&h->d_valT, static_cast<size_t>(h->nnz) * vb) != cudaSuccess) {
+                h->d_valT = nullptr;
+                return SPMV_ERR_ALLOC;
+            }
+            CK(launch_permute(h->d_val, h->d_perm, h->d_valT, h->nnz, h->vk, s));
+            h->valT_valid = true;
+        }
+        const bool ind = !h->valT_valid;
+        h->valT_requested = true;
         WarpOps ops;
         const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
         const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
         int ET = (meanT < 20.0) ? 7 : 15;
-        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, true, false, &ops)) ET = 15;
-        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, true, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) ET = 15;
+        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) return SPMV_ERR_UNSUPPORTED;
         ChunkTable *ct = get_chunks(h, ET, true);
         if (!ct) return SPMV_ERR_ALLOC;
         WarpParams wp{};
-        wp.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr};
+        wp.m = ind ? MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr}
+                   : MatRef{h->d_rowT, h->d_colT, h->d_valT, nullptr, g, grad_x, nullptr};
         wp.chunks = ct->d;
         wp.masks = ct->masks;
         wp.n_chunks = ct->n;

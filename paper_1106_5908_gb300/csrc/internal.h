@@ -88,6 +88,8 @@ cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk
                           int T, cudaStream_t s);
 
 // Halo gather: halo[h] = x[map[h]].
+// out[k] = val[perm[k]] for k < nnz (values of kind vk: FP64 or FP32).
+cudaError_t launch_permute(const void *val, const int32_t *perm, void *out, int64_t nnz, int vk, cudaStream_t s);
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
                           cudaStream_t s);
 

@@ -118,6 +118,44 @@ __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ x,
     }
 }
 
+// out[k] = val[perm[k]]: coalesced permutation and output, four gathers per
+// thread in flight.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_permute(const VT *__restrict__ val, const int32_t *__restrict__ perm,
+                                                 VT *__restrict__ out, int64_t n) {
+    const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x * 4;
+    for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * 4 + threadIdx.x; k0 < n; k0 += step) {
+        int32_t c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + static_cast<int64_t>(u) * blockDim.x;
+            c[u] = (k < n) ? __ldg(perm + k) : -1;
+        }
+        VT v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (c[u] >= 0) ? __ldg(val + c[u]) : VT(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t k = k0 + static_cast<int64_t>(u) * blockDim.x;
+            if (k < n) out[k] = v[u];
+        }
+    }
+}
+
+cudaError_t launch_permute(const void *val, const int32_t *perm, void *out, int64_t nnz, int vk, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (nnz + 1023) / 1024;
+    const int grid = static_cast<int>(want < 8LL * sms ? want : 8LL * sms);
+    if (vk == kF64)
+        k_permute<double><<<grid, 256, 0, s>>>(static_cast<const double *>(val), perm, static_cast<double *>(out), nnz);
+    else
+        k_permute<float><<<grid, 256, 0, s>>>(static_cast<const float *>(val), perm, static_cast<float *>(out), nnz);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
                           cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

@@ -124,6 +124,7 @@ class Matrix:
         abi.check(abi.spmv_set_accumulator(self._h, {"f64": 0, "ff": 1}[acc]), "spmv_set_accumulator")
 
     def set_values(self, val: torch.Tensor, stream=None) -> None:
+        self._values_token = None
         abi.check(abi.spmv_set_values(self._h, _dptr(val.contiguous()), _DT[val.dtype],
                                       _stream(stream)), "spmv_set_values")
 
@@ -292,6 +293,8 @@ class SpMVFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, val: torch.Tensor, x: torch.Tensor, A: Matrix, alpha: float = 1.0):
         A.set_values(val.detach())
+        ctx.token = object()
+        A._values_token = ctx.token  # the handle holds this forward's values
         y = A.apply(x.detach(), alpha=alpha)
         ctx.save_for_backward(val.detach(), x.detach())
         ctx.A = A
@@ -302,9 +305,10 @@ class SpMVFunction(torch.autograd.Function):
     def backward(ctx, gy: torch.Tensor):
         val, x = ctx.saved_tensors
         need_val, need_x = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        if need_x:
-            # the handle may hold other values by now (another forward ran)
+        if need_x and getattr(ctx.A, "_values_token", None) is not ctx.token:
+            # another forward (or set_values) replaced the handle's values since
             ctx.A.set_values(val)
+            ctx.A._values_token = ctx.token
         gx, gv = ctx.A.backward(gy.contiguous(), x, ctx.alpha, need_x=need_x, need_val=need_val)
         return gv, gx, None, None
 

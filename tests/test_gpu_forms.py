@@ -72,6 +72,35 @@ def test_backward_small(alpha):
         assert_within(host(gv), rgv, np.abs(rgv), 2.5e-16, "grad_val")
 
 
+def test_backward_after_new_values():
+    """The transposed values are rebuilt after spmv_set_values, and an autograd
+    graph whose forward ran before another one still uses its own values."""
+    from paper_1106_5908_gb300 import spmv
+    A = W.random_csr(2000, 1800, seed=21, max_len=25)
+    M = make(A)
+    x = W.uniform(A.n_cols, 3)
+    g = W.uniform(A.n_rows, 4)
+    M.backward(dev(g), dev(x))
+    v2 = W.uniform(A.nnz, 5)
+    M.set_values(dev(v2))
+    for _ in range(2):  # rebuilt once, then reused
+        gx, _ = M.backward(dev(g), dev(x), need_val=False)
+        rgx, _, bound = oracle.backward(A.row_ptr, A.col_idx, v2, A.n_cols, g, x, with_bound=True)
+        assert_within(host(gx), rgx, bound, 1e-13, "grad_x after set_values")
+    val1 = dev(A.val).requires_grad_(False)
+    val2 = dev(v2).requires_grad_(False)
+    xa = dev(x).requires_grad_(True)
+    xb = dev(x).requires_grad_(True)
+    y1 = spmv(M, val1, xa)
+    y2 = spmv(M, val2, xb)
+    y1.backward(dev(g))
+    y2.backward(dev(g))
+    r1, _, b1 = oracle.backward(*A.astuple(), A.n_cols, g, x, with_bound=True)
+    r2, _, b2 = oracle.backward(A.row_ptr, A.col_idx, v2, A.n_cols, g, x, with_bound=True)
+    assert_within(host(xa.grad), r1, b1, 1e-13, "first graph")
+    assert_within(host(xb.grad), r2, b2, 1e-13, "second graph")
+
+
 @pytest.fixture(scope="module")
 def c5():
     return W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
