@@ -544,6 +544,60 @@ def run_only_plain(args, local_rank):
                       "GBs": model.bytes_plain(A.n_rows, A.n_cols, A.nnz) / ms / 1e6}), flush=True)
 
 
+def run_ordering_study(args, local_rank):
+    """The ordering study (the paper's RCM remark, Sect. 2): the plain FP64 product
+    on the Hamiltonian-like matrix in its natural order, in reverse Cuthill-McKee
+    order and in a random order (P A P^T with x permuted alike), each with the
+    autotuned plan and two fixed ones.  Prints one JSON line (not the benchmark
+    line).  Under ncu, the DRAM and L2 byte counters of these launches give kappa
+    at both levels."""
+    import torch
+    from paper_1106_5908_gb300 import Matrix
+    from paper_1106_5908_gb300.build import build as build_lib
+    torch.cuda.set_device(local_rank)
+    build_lib()
+    A, x = c2_workload()
+    # per-row tolerance scale sum_j |a_ij x_j| of the natural order
+    scale = np.add.reduceat(np.abs(A.val) * np.abs(x[A.col_idx]), A.row_ptr[:-1].astype(np.int64))
+    y_nat = None
+    out = {}
+    for name in ("natural", "rcm", "random"):
+        order = None if name == "natural" else (W.rcm_order(A) if name == "rcm" else W.random_order(A.n_rows))
+        B = A if order is None else W.permute_symmetric(A, order)
+        M = Matrix.from_csr(B.row_ptr, B.col_idx, B.val, B.n_cols)
+        xd = torch.as_tensor(x if order is None else x[order]).cuda()
+        y = torch.empty(B.n_rows, dtype=torch.float64, device="cuda")
+        auto = M.info()
+        res = {"bandwidth": W.bandwidth(B), "plan": {"family": auto["family"], "E": auto["E"]}}
+        plans = (("auto", None), ("two_stage_E7", (0, 7)), ("three_stage_E15", (3, 15)))
+        for label, plan in (plans[:1] if args.study_auto_only else plans):
+            if plan is not None:
+                M.set_plan(*plan)
+            for _ in range(args.warmup):
+                M.apply(xd, y)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                M.apply(xd, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            res[label] = {"ms": ms, "GBs": model.bytes_plain(B.n_rows, B.n_cols, B.nnz) / ms / 1e6}
+        # the reordered product is the reordered natural product
+        yh = y.cpu().numpy()
+        if order is None:
+            y_nat = yh
+        else:
+            ref = y_nat[order]
+            res["max_diff_over_row_scale_vs_natural"] = float(np.max(np.abs(yh - ref) / scale[order]))
+        out[name] = res
+        del M, xd, y
+    print(json.dumps({"study": "ordering", "workload": f"Hamiltonian-like N={A.n_rows} nnz={A.nnz}",
+                      "steps": args.steps, "warmup": args.warmup, "orderings": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,6 +607,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--only", choices=("plain",), default=None,
                     help="run only the plain FP64 product (for kernel profiling)")
+    ap.add_argument("--study", choices=("ordering",), default=None,
+                    help="natural / RCM / random ordering of the Hamiltonian-like matrix")
+    ap.add_argument("--study-auto-only", action="store_true",
+                    help="ordering study: the autotuned plan only (the ncu capture case)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -564,6 +622,9 @@ def main():
         return
     if args.only == "plain":
         run_only_plain(args, local_rank)
+        return
+    if args.study == "ordering":
+        run_ordering_study(args, local_rank)
         return
     if world > 1:
         import torch

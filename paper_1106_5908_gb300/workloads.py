@@ -261,6 +261,40 @@ def batch_matrix(m: int, n: int, seed: int = SEED_C4_BATCH) -> CRS:
     return hamiltonian_like(int(n), seed=seed * 1000 + m)
 
 
+# Orderings for the ordering study (the paper's RCM remark, Sect. 2): the
+# matrix P A P^T, where row/column i of the result is row/column order[i] of A.
+SEED_ORDER_RANDOM = 6601
+
+
+def rcm_order(A: CRS) -> np.ndarray:
+    """Reverse Cuthill-McKee order of the (symmetric) pattern of A."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    M = sp.csr_matrix((np.ones(A.nnz, np.int8), A.col_idx, A.row_ptr), shape=(A.n_rows, A.n_cols))
+    return np.asarray(reverse_cuthill_mckee(M, symmetric_mode=True), dtype=np.int64)
+
+
+def random_order(n: int, seed: int = SEED_ORDER_RANDOM) -> np.ndarray:
+    return np.random.default_rng(seed).permutation(n)
+
+
+def permute_symmetric(A: CRS, order: np.ndarray) -> CRS:
+    """P A P^T: entry (i, j) of the result is entry (order[i], order[j]) of A;
+    columns sorted within each row."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.col_idx, A.row_ptr), shape=(A.n_rows, A.n_cols))
+    order = np.asarray(order, dtype=np.int64)
+    P = M[order][:, order].tocsr()
+    P.sort_indices()
+    return CRS(P.indptr.astype(np.int32), P.indices.astype(np.int32), P.data.astype(A.val.dtype), A.n_cols)
+
+
+def bandwidth(A: CRS) -> int:
+    """max |i - j| over the entries (i, j)."""
+    rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr.astype(np.int64)))
+    return int(np.abs(rows - A.col_idx).max()) if A.nnz else 0
+
+
 # Shapes of the five synthetic configurations.
 C1_GRID = 256          # 2D 5-point, N = 65,536
 C2_N = 4_194_304       # Hamiltonian-like, N = 4,194,304

@@ -236,6 +236,33 @@ def test_batched_small(dtype):
             assert_within(host(yd[m]), ref, bound, rel, f"batch m={m} rep={rep}")
 
 
+def test_batched_256_full_size():
+    """The benchmark's batch at full size: 256 matrices, N ~ U[1000, 200000]
+    (5-point Laplacians and Hamiltonian-like patterns, 235 M entries), one
+    persistent launch replayed from a CUDA graph; every result against the
+    oracle, for two right-hand sides (the second replay reuses the graph)."""
+    from paper_1106_5908_gb300 import Batch, Matrix
+    sizes = W.batch_sizes(W.C4_COUNT)
+    As, mats = [], []
+    for m, n in enumerate(sizes):
+        A = W.batch_matrix(m, int(n))
+        As.append(A)
+        mats.append(Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols))
+    assert len(As) == 256 and sum(A.nnz for A in As) > 2e8
+    B = Batch(mats)
+    ys = [torch.empty(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+    xd = [torch.empty(A.n_cols, dtype=torch.float64, device="cuda") for A in As]
+    for rep in range(2):  # same buffers: the second apply replays the captured graph
+        xs = [W.uniform(A.n_cols, 1000 * rep + m) for m, A in enumerate(As)]
+        for m in range(len(As)):
+            xd[m].copy_(torch.as_tensor(xs[m]))
+        B.apply(xd, ys)
+        torch.cuda.synchronize()
+        for m, A in enumerate(As):
+            ref, bound = oracle.spmv(*A.astuple(), xs[m], with_bound=True)
+            assert_within(host(ys[m]), ref, bound, 1e-13, f"batch m={m} rep={rep}")
+
+
 def test_batched_integer_bitexact():
     from paper_1106_5908_gb300 import Batch, Matrix
     As = [W.random_csr(n, n, seed=n, integer=True, max_len=20, long_rows=1, long_len=min(n, 4000))
