@@ -298,6 +298,24 @@ spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32
  * SPMV_OK otherwise. */
 spmv_status spmv_check_device_error(spmv_handle h, void *stream);
 
+/* Check a CRS structure held in DEVICE memory on the device (the checks
+ * spmv_create applies on the host): row_ptr[0] == 0, row_ptr nondecreasing,
+ * row_ptr[n_rows] == nnz, 0 <= col_idx[k] < n_cols.  row_ptr has n_rows + 1
+ * entries and col_idx nnz; only those are read, whatever their values, and a
+ * violation is recorded in a device word (no trap).  Synchronises stream.
+ * Returns SPMV_ERR_INVALID_INDEX on a violation, SPMV_ERR_INVALID_ARG for
+ * negative sizes, nnz >= 2^31 or null pointers. */
+spmv_status spmv_validate_device(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col_idx, void *stream);
+
+/* Self-test of the failure detection: one warp waits on an on-device barrier
+ * that nothing completes, with a wall-time limit of limit_ns (1 us .. 1 s, the
+ * limit every on-device wait of the library uses); the wait gives up, records
+ * the timeout in the handle's error word and the kernel returns, leaving the
+ * context usable.  Synchronises stream; returns SPMV_ERR_TIMEOUT when the path
+ * works (then the error word is clear again). */
+spmv_status spmv_selftest_wait_timeout(spmv_handle h, int64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ EXPORTS = (
     "spmv_split_get_halo",
     "spmm_apply", "spmv_backward", "spmv_get_transpose", "spmv_transpose_noalloc", "spmv_batched_create",
     "spmv_batched_destroy", "spmv_batched_apply", "spmv_batched_get_info", "spmv_ir_cg",
-    "spmv_cg", "spmv_check_device_error",
+    "spmv_cg", "spmv_check_device_error", "spmv_validate_device", "spmv_selftest_wait_timeout",
 )
 
 
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
         "spmv_ir_cg": (st, [vp, vp, vp, f64, i32, f64, i32, vp, vp]),
         "spmv_cg": (st, [vp, vp, vp, f64, i32, vp, vp]),
         "spmv_check_device_error": (st, [vp, vp]),
+        "spmv_validate_device": (st, [i32, i32, i64, vp, vp, vp]),
+        "spmv_selftest_wait_timeout": (st, [vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -146,4 +148,6 @@ spmv_batched_get_info = _fwd("spmv_batched_get_info")
 spmv_ir_cg = _fwd("spmv_ir_cg")
 spmv_cg = _fwd("spmv_cg")
 spmv_check_device_error = _fwd("spmv_check_device_error")
+spmv_validate_device = _fwd("spmv_validate_device")
+spmv_selftest_wait_timeout = _fwd("spmv_selftest_wait_timeout")
 spmv_status_string = _fwd("spmv_status_string")

@@ -1517,6 +1517,31 @@ spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_t
     return converged ? SPMV_OK : SPMV_ERR_NOT_CONVERGED;
 }
 
+spmv_status spmv_validate_device(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *row_ptr,
+                                 const int32_t *col_idx, void *stream) {
+    if (n_rows < 0 || n_cols < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return SPMV_ERR_INVALID_ARG;
+    if (!row_ptr || (nnz > 0 && !col_idx)) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int32_t *bad = nullptr;
+    if (dmalloc(&bad, 1) != cudaSuccess) return SPMV_ERR_ALLOC;
+    int32_t v = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, 4, s);
+    if (e == cudaSuccess) e = launch_validate(n_rows, n_cols, nnz, row_ptr, col_idx, bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(bad);
+    if (e != cudaSuccess) return SPMV_ERR_CUDA;
+    return v ? SPMV_ERR_INVALID_INDEX : SPMV_OK;
+}
+
+spmv_status spmv_selftest_wait_timeout(spmv_handle h, int64_t limit_ns, void *stream) {
+    if (!h || limit_ns < 1000 || limit_ns > static_cast<int64_t>(kWaitLimitNs)) return SPMV_ERR_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(launch_wait_timeout(static_cast<uint64_t>(limit_ns), h->d_err, s));
+    return spmv_check_device_error(h, stream);
+}
+
 spmv_status spmv_check_device_error(spmv_handle h, void *stream) {
     if (!h) return SPMV_ERR_INVALID_ARG;
     DeviceGuard dg(h->device);

@@ -73,17 +73,20 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
-// Wait for phase `parity` of `bar` to complete.  Gives up after kWaitLimitNs of
-// wall time (or kWaitLimitIters polls) and returns false; never spins forever.
+// Wait for phase `parity` of `bar` to complete.  Gives up after limit_ns of wall
+// time (checked every 64 polls), or after kWaitLimitIters polls should the timer
+// not advance, and returns false; never spins forever.  A poll returns after at
+// most kTryWaitSuspendNs, so the poll bound is at most ~80 s.
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
-constexpr uint32_t kWaitLimitIters = 1u << 26;
+constexpr uint32_t kWaitLimitIters = 1u << 22;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 0; it < kWaitLimitIters; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 255u && global_timer_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

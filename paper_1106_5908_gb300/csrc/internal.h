@@ -90,6 +90,12 @@ cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk
 // Halo gather: halo[h] = x[map[h]].
 // out[k] = val[perm[k]] for k < nnz (values of kind vk: FP64 or FP32).
 cudaError_t launch_permute(const void *val, const int32_t *perm, void *out, int64_t nnz, int vk, cudaStream_t s);
+// Device-side CRS check; sets *bad to 1 on any violation.
+cudaError_t launch_validate(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp, const int32_t *col,
+                            int32_t *bad, cudaStream_t s);
+// One warp waits on an mbarrier nothing completes, for limit_ns, then records
+// kDevErrTimeout in *err.
+cudaError_t launch_wait_timeout(uint64_t limit_ns, int32_t *err, cudaStream_t s);
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
                           cudaStream_t s);
 

@@ -556,4 +556,59 @@ cudaError_t launch_convert(const void *src, int sk, void *dst, int dk, int64_t n
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Failure detection
+// ---------------------------------------------------------------------------
+
+static int elementwise_grid(int64_t n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + 255) / 256;
+    return static_cast<int>(want < 16LL * sms ? want : 16LL * sms);
+}
+
+// Device-side CRS check: row_ptr[0] == 0, nondecreasing, row_ptr[n_rows] == nnz,
+// 0 <= col < n_cols.  Every read stays inside [0, n_rows] of row_ptr and [0, nnz)
+// of col_idx whatever their contents; a violation sets *bad (no trap).
+__global__ void __launch_bounds__(256) k_validate(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                                  const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ col, int32_t *bad) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t == 0 && (__ldg(rp) != 0 || static_cast<int64_t>(__ldg(rp + n_rows)) != nnz)) atomicExch(bad, 1);
+    for (int64_t i = t; i < n_rows; i += stride)
+        if (__ldg(rp + i + 1) < __ldg(rp + i)) atomicExch(bad, 1);
+    for (int64_t k = t; k < nnz; k += stride) {
+        const int32_t c = __ldg(col + k);
+        if (c < 0 || c >= n_cols) atomicExch(bad, 1);
+    }
+}
+
+cudaError_t launch_validate(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp, const int32_t *col,
+                            int32_t *bad, cudaStream_t s) {
+    const int64_t work = (static_cast<int64_t>(n_rows) > nnz) ? n_rows : nnz;
+    k_validate<<<elementwise_grid(work > 0 ? work : 1), 256, 0, s>>>(n_rows, n_cols, nnz, rp, col, bad);
+    return cudaGetLastError();
+}
+
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// arrives on, with a wall-time limit of limit_ns; the wait gives up, the kernel
+// records the timeout in *err and returns.  No copy is in flight on the barrier.
+__global__ void k_wait_timeout(uint64_t limit_ns, int32_t *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) set_error(err, kDevErrTimeout);
+}
+
+cudaError_t launch_wait_timeout(uint64_t limit_ns, int32_t *err, cudaStream_t s) {
+    k_wait_timeout<<<1, 32, 0, s>>>(limit_ns, err);
+    return cudaGetLastError();
+}
+
 }  // namespace spmv
