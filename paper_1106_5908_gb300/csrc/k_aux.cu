@@ -171,8 +171,10 @@ cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int
 // grad_val over the warp chunks of A: lanes take 32 consecutive entries at a
 // time (coalesced column loads and gradient stores); the row of each entry is the
 // chunk's first row plus the row starts (bits of the chunk's bitmask) up to it.
+// The kernel waits on its gathers, so it is held to three blocks (24 warps) per
+// SM (223 -> 181 us on the 27-point 128^3 pattern against two blocks).
 template <typename VT>
-__global__ void __launch_bounds__(256) k_grad_val_chunks(const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(256, 3) k_grad_val_chunks(const int32_t *__restrict__ rp,
                                                          const int32_t *__restrict__ col,
                                                          const ChunkDesc *__restrict__ chunks,
                                                          const uint32_t *__restrict__ masks, int mwp,
