@@ -589,6 +589,8 @@ spmv_status ensure_cg(spmv_matrix *h, bool mixed) {
         w.n = n;
         if (dmalloc(&w.sc, kScCount) != cudaSuccess) return SPMV_ERR_ALLOC;
         if (dmalloc(&w.partials, static_cast<size_t>(cg_partials_len())) != cudaSuccess) return SPMV_ERR_ALLOC;
+        // the reductions' ticket word (after the partials) starts at zero
+        if (cudaMemset(w.partials, 0, static_cast<size_t>(cg_partials_len()) * 8) != cudaSuccess) return SPMV_ERR_CUDA;
         if (cudaMallocHost(reinterpret_cast<void **>(&w.host), 8 * sizeof(double)) != cudaSuccess) return SPMV_ERR_ALLOC;
         if (dmalloc(&w.r64, n) != cudaSuccess) return SPMV_ERR_ALLOC;
     }

@@ -1,6 +1,9 @@
-// Vector kernels of the conjugate-gradient solvers: FP64-accumulated dot
-// products with a deterministic two-stage reduction, fused CG updates in FP32
-// (inner solver) and FP64 (outer residual, update, and the FP64 reference CG).
+// Vector kernels of the conjugate-gradient solvers: dot products and fused CG
+// updates in FP32 (inner solver) and FP64 (outer residual, update, and the FP64
+// reference CG).  Reductions run on two blocks per SM; each block stores its
+// partial sum and the last block to finish (an atomic ticket, no waiting) sums
+// the partials in block order and applies the scalar step, so the result is
+// deterministic and no separate reduction launch is needed.
 #include <algorithm>
 #include <cstdint>
 
@@ -27,17 +30,59 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
     return t;  // valid in thread 0
 }
 
+// Where a reduction ends: partials[gridDim.x], the ticket counting finished
+// blocks (zero between launches) and the scalar step op applied to the sum.
+struct RedOut {
+    double *partials;
+    unsigned int *ticket;
+    double *sc;
+    int op;
+    int dst;
+};
+
+__device__ __forceinline__ void apply_op(double t, double *sc, int op, int dst) {
+    if (op == kOpStore) {
+        sc[dst] = t;
+    } else if (op == kOpAlpha) {  // t = p.q; a zero direction (converged) takes no step
+        sc[kScPQ] = t;
+        sc[kScAlpha] = (t != 0.0) ? sc[kScRho] / t : 0.0;
+    } else if (op == kOpBeta) {   // t = r_new.r_new
+        sc[kScBeta] = (sc[kScRho] != 0.0) ? t / sc[kScRho] : 0.0;
+        sc[kScRho] = t;
+    }
+}
+
+// t: the block's partial (valid in thread 0).  The last block sums all partials
+// in block order, applies the step and re-arms the ticket.
+__device__ __forceinline__ void finish(double t, const RedOut &o, double *s_red) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        o.partials[blockIdx.x] = t;
+        __threadfence();
+        s_last = (atomicAdd(o.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += blockDim.x) acc += __ldcg(o.partials + i);
+    const double tot = block_sum(acc, s_red);
+    if (threadIdx.x == 0) {
+        apply_op(tot, o.sc, o.op, o.dst);
+        *o.ticket = 0u;
+    }
+}
+
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(kDotThreads) k_dot(const TA *__restrict__ a,
                                                      const TB *__restrict__ b, int64_t n,
-                                                     double *__restrict__ partials) {
+                                                     const RedOut o) {
     __shared__ double s_red[32];
     double acc = 0.0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
         acc = fma(widen(a[i]), widen(b[i]), acc);
-    const double t = block_sum(acc, s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    finish(block_sum(acc, s_red), o, s_red);
 }
 
 // Vectorised variants for 16-byte aligned operands: four floats (or two
@@ -49,11 +94,12 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_f32v(const float4 *__restri
                                                           const float4 *__restrict__ b, int64_t n4,
                                                           const float *__restrict__ at,
                                                           const float *__restrict__ bt, int tail,
-                                                          double *__restrict__ partials) {
+                                                          const RedOut o) {
     __shared__ double s_red[32];
     AccFF c0, c1, c2, c3;
     c0.zero(); c1.zero(); c2.zero(); c3.zero();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+#pragma unroll 4
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
         const float4 u = __ldg(a + i), v = __ldg(b + i);
         c0.fma(u.x, v.x);
@@ -62,46 +108,25 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_f32v(const float4 *__restri
         c3.fma(u.w, v.w);
     }
     if (blockIdx.x == 0 && threadIdx.x < tail) c0.fma(at[threadIdx.x], bt[threadIdx.x]);
-    const double t = block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    finish(block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red), o, s_red);
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_dot_f64v(const double2 *__restrict__ a,
                                                           const double2 *__restrict__ b, int64_t n2,
                                                           const double *__restrict__ at,
                                                           const double *__restrict__ bt, int tail,
-                                                          double *__restrict__ partials) {
+                                                          const RedOut o) {
     __shared__ double s_red[32];
     double c0 = 0.0, c1 = 0.0;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+#pragma unroll 4
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n2; i += stride) {
         const double2 u = __ldg(a + i), v = __ldg(b + i);
         c0 = fma(u.x, v.x, c0);
         c1 = fma(u.y, v.y, c1);
     }
     if (blockIdx.x == 0 && threadIdx.x < tail) c0 = fma(at[threadIdx.x], bt[threadIdx.x], c0);
-    const double t = block_sum(c0 + c1, s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
-}
-
-// Sum the partials in a fixed order and apply the scalar step `op`.
-__global__ void __launch_bounds__(kDotThreads) k_reduce(const double *__restrict__ partials,
-                                                        int32_t np, double *sc, int op, int dst) {
-    __shared__ double s_red[32];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) acc += partials[i];
-    const double t = block_sum(acc, s_red);
-    if (threadIdx.x == 0) {
-        if (op == kOpStore) {
-            sc[dst] = t;
-        } else if (op == kOpAlpha) {  // t = p.q; a zero direction (converged) takes no step
-            sc[kScPQ] = t;
-            sc[kScAlpha] = (t != 0.0) ? sc[kScRho] / t : 0.0;
-        } else if (op == kOpBeta) {   // t = r_new.r_new
-            sc[kScBeta] = (sc[kScRho] != 0.0) ? t / sc[kScRho] : 0.0;
-            sc[kScRho] = t;
-        }
-    }
+    finish(block_sum(c0 + c1, s_red), o, s_red);
 }
 
 // Inner (FP32) update: d += a*p, r -= a*q, partial sums of r.r (FP64 accumulate).
@@ -110,7 +135,7 @@ __global__ void __launch_bounds__(kDotThreads) k_update32(float *__restrict__ d,
                                                           const float *__restrict__ p,
                                                           const float *__restrict__ q,
                                                           const double *__restrict__ sc, int64_t n,
-                                                          double *__restrict__ partials) {
+                                                          const RedOut o) {
     __shared__ double s_red[32];
     const float a = __double2float_rn(sc[kScAlpha]);
     double acc = 0.0;
@@ -122,8 +147,7 @@ __global__ void __launch_bounds__(kDotThreads) k_update32(float *__restrict__ d,
         const double rw = widen(ri);
         acc = fma(rw, rw, acc);
     }
-    const double t = block_sum(acc, s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    finish(block_sum(acc, s_red), o, s_red);
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_update32v(float4 *__restrict__ d, float4 *__restrict__ r,
@@ -133,12 +157,13 @@ __global__ void __launch_bounds__(kDotThreads) k_update32v(float4 *__restrict__ 
                                                            float *__restrict__ dt, float *__restrict__ rt,
                                                            const float *__restrict__ pt,
                                                            const float *__restrict__ qt, int tail,
-                                                           double *__restrict__ partials) {
+                                                           const RedOut o) {
     __shared__ double s_red[32];
     const float a = __double2float_rn(sc[kScAlpha]);
     AccFF c0, c1, c2, c3;
     c0.zero(); c1.zero(); c2.zero(); c3.zero();
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+#pragma unroll 2
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
         const float4 pv = p[i], qv = q[i];
         float4 dv = d[i], rv = r[i];
@@ -160,8 +185,7 @@ __global__ void __launch_bounds__(kDotThreads) k_update32v(float4 *__restrict__ 
         rt[j] = ri;
         c0.fma(ri, ri);
     }
-    const double t = block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    finish(block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red), o, s_red);
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_direction32v(float4 *__restrict__ p,
@@ -187,19 +211,30 @@ __global__ void __launch_bounds__(kDotThreads) k_update64(double *__restrict__ x
                                                           const double *__restrict__ p,
                                                           const double *__restrict__ q,
                                                           const double *__restrict__ sc, int64_t n,
-                                                          double *__restrict__ partials) {
+                                                          const RedOut o) {
     __shared__ double s_red[32];
     const double a = sc[kScAlpha];
-    double acc = 0.0;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double acc0 = 0.0, acc1 = 0.0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {  // two independent elements in flight
+        const double p0 = p[i], q0 = q[i], x0 = x[i], r0 = r[i];
+        const double p1 = p[i + stride], q1 = q[i + stride], x1 = x[i + stride], r1 = r[i + stride];
+        x[i] = fma(a, p0, x0);
+        x[i + stride] = fma(a, p1, x1);
+        const double ri0 = fma(-a, q0, r0), ri1 = fma(-a, q1, r1);
+        r[i] = ri0;
+        r[i + stride] = ri1;
+        acc0 = fma(ri0, ri0, acc0);
+        acc1 = fma(ri1, ri1, acc1);
+    }
+    if (i < n) {
         x[i] = fma(a, p[i], x[i]);
         const double ri = fma(-a, q[i], r[i]);
         r[i] = ri;
-        acc = fma(ri, ri, acc);
+        acc0 = fma(ri, ri, acc0);
     }
-    const double t = block_sum(acc, s_red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    finish(block_sum(acc0 + acc1, s_red), o, s_red);
 }
 
 template <typename T>
@@ -229,82 +264,86 @@ __global__ void __launch_bounds__(kDotThreads) k_axpy_64_32(double *__restrict__
         x[i] = fma(s, widen(d[i]), x[i]);
 }
 
-static int vec_grid(int64_t n) {
+static int sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads, 16LL * sms)));
+    return sms;
 }
 
-int cg_partials_len() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return 16 * sms;
+// elementwise kernels: up to 16 blocks per SM
+static int vec_grid(int64_t n) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads,
+                                                                   16LL * sm_count())));
+}
+
+// reductions: up to kRedBlocksPerSM blocks per SM (each block's FP64 tree work
+// is paid once per block, so fewer, longer-running blocks)
+constexpr int kRedBlocksPerSM = 2;
+static int red_grid(int64_t n) {
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kDotThreads - 1) / kDotThreads,
+                                                                   int64_t(kRedBlocksPerSM) * sm_count())));
+}
+
+// partials (one per reduction block) followed by the ticket word
+int cg_partials_len() { return kRedBlocksPerSM * sm_count() + 2; }
+
+static RedOut red_out(double *partials, double *sc, int op, int dst) {
+    return RedOut{partials, reinterpret_cast<unsigned int *>(partials + kRedBlocksPerSM * sm_count()), sc, op,
+                  dst};
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 cudaError_t cg_dot(const void *a, int ak, const void *b, int bk, int64_t n, double *partials,
                    double *sc, int op, int dst, cudaStream_t s) {
-    int grid;
+    const RedOut o = red_out(partials, sc, op, dst);
     if (ak == kF64 && bk == kF64) {
         const double *ad = static_cast<const double *>(a), *bd = static_cast<const double *>(b);
         if (aligned16(a) && aligned16(b)) {
             const int64_t n2 = n / 2;
-            grid = vec_grid(n2);
-            k_dot_f64v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<const double2 *>(ad),
-                                                    reinterpret_cast<const double2 *>(bd), n2,
-                                                    ad + 2 * n2, bd + 2 * n2, static_cast<int>(n - 2 * n2),
-                                                    partials);
+            k_dot_f64v<<<red_grid(n2), kDotThreads, 0, s>>>(reinterpret_cast<const double2 *>(ad),
+                                                            reinterpret_cast<const double2 *>(bd), n2,
+                                                            ad + 2 * n2, bd + 2 * n2,
+                                                            static_cast<int>(n - 2 * n2), o);
         } else {
-            grid = vec_grid(n);
-            k_dot<double, double><<<grid, kDotThreads, 0, s>>>(ad, bd, n, partials);
+            k_dot<double, double><<<red_grid(n), kDotThreads, 0, s>>>(ad, bd, n, o);
         }
     } else if (ak == kF32 && bk == kF32) {
         const float *af = static_cast<const float *>(a), *bf = static_cast<const float *>(b);
         if (aligned16(a) && aligned16(b)) {
             const int64_t n4 = n / 4;
-            grid = vec_grid(n4);
-            k_dot_f32v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<const float4 *>(af),
-                                                    reinterpret_cast<const float4 *>(bf), n4,
-                                                    af + 4 * n4, bf + 4 * n4, static_cast<int>(n - 4 * n4),
-                                                    partials);
+            k_dot_f32v<<<red_grid(n4), kDotThreads, 0, s>>>(reinterpret_cast<const float4 *>(af),
+                                                            reinterpret_cast<const float4 *>(bf), n4,
+                                                            af + 4 * n4, bf + 4 * n4,
+                                                            static_cast<int>(n - 4 * n4), o);
         } else {
-            grid = vec_grid(n);
-            k_dot<float, float><<<grid, kDotThreads, 0, s>>>(af, bf, n, partials);
+            k_dot<float, float><<<red_grid(n), kDotThreads, 0, s>>>(af, bf, n, o);
         }
     } else {
         return cudaErrorInvalidValue;
     }
-    k_reduce<<<1, kDotThreads, 0, s>>>(partials, grid, sc, op, dst);
     return cudaGetLastError();
 }
 
 cudaError_t cg_update32(float *d, float *r, const float *p, const float *q, int64_t n,
                         double *partials, double *sc, cudaStream_t s) {
-    int grid;
+    const RedOut o = red_out(partials, sc, kOpBeta, 0);
     if (aligned16(d) && aligned16(r) && aligned16(p) && aligned16(q)) {
         const int64_t n4 = n / 4;
-        grid = vec_grid(n4);
-        k_update32v<<<grid, kDotThreads, 0, s>>>(reinterpret_cast<float4 *>(d), reinterpret_cast<float4 *>(r),
-                                                 reinterpret_cast<const float4 *>(p),
-                                                 reinterpret_cast<const float4 *>(q), sc, n4, d + 4 * n4,
-                                                 r + 4 * n4, p + 4 * n4, q + 4 * n4,
-                                                 static_cast<int>(n - 4 * n4), partials);
+        k_update32v<<<red_grid(n4), kDotThreads, 0, s>>>(
+            reinterpret_cast<float4 *>(d), reinterpret_cast<float4 *>(r), reinterpret_cast<const float4 *>(p),
+            reinterpret_cast<const float4 *>(q), sc, n4, d + 4 * n4, r + 4 * n4, p + 4 * n4, q + 4 * n4,
+            static_cast<int>(n - 4 * n4), o);
     } else {
-        grid = vec_grid(n);
-        k_update32<<<grid, kDotThreads, 0, s>>>(d, r, p, q, sc, n, partials);
+        k_update32<<<red_grid(n), kDotThreads, 0, s>>>(d, r, p, q, sc, n, o);
     }
-    k_reduce<<<1, kDotThreads, 0, s>>>(partials, grid, sc, kOpBeta, 0);
     return cudaGetLastError();
 }
 
 cudaError_t cg_update64(double *x, double *r, const double *p, const double *q, int64_t n,
                         double *partials, double *sc, cudaStream_t s) {
-    const int grid = vec_grid(n);
-    k_update64<<<grid, kDotThreads, 0, s>>>(x, r, p, q, sc, n, partials);
-    k_reduce<<<1, kDotThreads, 0, s>>>(partials, grid, sc, kOpBeta, 0);
+    k_update64<<<red_grid(n), kDotThreads, 0, s>>>(x, r, p, q, sc, n, red_out(partials, sc, kOpBeta, 0));
     return cudaGetLastError();
 }
 

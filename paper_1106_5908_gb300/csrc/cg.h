@@ -10,6 +10,7 @@ enum : int { kScRho = 0, kScPQ = 1, kScAlpha = 2, kScBeta = 3, kScNorm = 4, kScC
 // Scalar steps applied after a reduction.
 enum : int { kOpStore = 0, kOpAlpha = 1, kOpBeta = 2 };
 
+// doubles of the reduction work array (partials and the ticket word; zero it once)
 int cg_partials_len();
 // sc[dst] = a.b (op kOpStore) or alpha = sc[rho]/(a.b) (op kOpAlpha).  FP64 accumulation.
 cudaError_t cg_dot(const void *a, int ak, const void *b, int bk, int64_t n, double *partials,
