@@ -161,7 +161,7 @@ def test_c2_fp32_storage(c2, acc):
     assert_within(host(M.apply(dev(x32), out_dtype=torch.float64)), ref, bound, 1e-6, f"C2 fp32 y64 {acc}")
 
 
-@pytest.mark.parametrize("nrhs", [4, 32])
+@pytest.mark.parametrize("nrhs", [4, 8, 16, 32])
 def test_c2_block_vectors(c2, m2, nrhs):
     A, _, _, _ = c2
     X = W.uniform(0, W.SEED_C4_X, shape=(A.n_rows, nrhs))
