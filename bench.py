@@ -140,6 +140,11 @@ def c2_workload():
     return A, x
 
 
+def workload_desc(n, nnz, total_halo):
+    return (f"Hamiltonian-like N={n} nnz={nnz} (stand-in for HMeP): plain FP64 + split over 8 blocks "
+            f"(halo {total_halo}) + FP32-storage")
+
+
 def step_bytes(A, total_halo):
     n, nnz = A.n_rows, A.nnz
     b_plain = model.bytes_plain(n, n, nnz)
@@ -181,7 +186,7 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"Hamiltonian-like N={n} nnz={nnz}: plain + split(8) + FP32-storage",
+        "config": {"workload": workload_desc(n, nnz, int(cnt.sum())), "n_rows": n, "nnz": nnz,
                    "parallelism": "host cores (OpenMP over rows)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"full matrix, {args.steps} steps of three FP64 row-sum passes"},
@@ -393,8 +398,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": (f"Hamiltonian-like N={n} nnz={nnz} (stand-in for HMeP): plain FP64 "
-                                f"+ split over 8 blocks (halo {total_halo}, 2 streams) + FP32-storage"),
+        "config": {"workload": workload_desc(n, nnz, total_halo), "split_streams": 2,
                    "n_rows": n, "nnz": nnz, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (matrix 657 MB vs 126 MB L2), no flush",
                    "plan": info},
