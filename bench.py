@@ -46,7 +46,8 @@ TRAFFIC = {"kernel_hash": "03c82c1b5b9f0b53", "bytes_per_launch": 708644011,
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("pipe_kernel.cuh", "warp_kernel.cuh", "common.cuh", "internal.h", "k_warp_f64.cu"):
+    for f in ("slot_kernel.cuh", "k_slot.cu", "pipe_kernel.cuh", "warp_kernel.cuh", "common.cuh", "internal.h",
+              "k_warp_f64.cu"):
         with open(os.path.join(ROOT, "paper_1106_5908_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -405,8 +406,8 @@ def run_ours(args, rank, world, local_rank):
         "gflops": flops_step * K * world / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                     "kernel": (f"{'k_pipe3' if info['family'] == 3 else 'k_pipe'}<{info['E']},f64> plain FP64 "
-                                "product (autotuned warp-chunk kernel)"),
+                     "kernel": (f"{ {0: 'k_pipe', 3: 'k_pipe3', 4: 'k_slot'}.get(info['family'], 'k_tile')}"
+                                f"<{info['E']},f64> plain FP64 product (autotuned warp-chunk kernel)"),
                      "peak_source": peaks["source"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "frac_of_8tbs_spec": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": b_plain},

@@ -89,10 +89,12 @@ void spmv_destroy(spmv_handle h);
  * storage or FP32 -> FP64 storage (converted on the device).  Asynchronous. */
 spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *stream);
 
-/* Shape and plan of a handle.  plan[0..7] receives: kernel family (0 = nnz-split
- * tile kernel, 1 = row-vector kernel), nonzeros per thread E, threads per CTA,
- * number of tiles, rows per tile cap, threads per row for the row-vector kernel,
- * number of rows longer than a tile, value dtype.  Any output may be NULL. */
+/* Shape and plan of a handle.  plan[0..7] receives: kernel family (as for
+ * spmv_set_plan), entries per lane or thread segment E, threads per CTA, number
+ * of chunks or tiles, rows per chunk or tile cap, threads per row of the
+ * row-vector kernel, number of rows longer than a chunk or tile, value dtype.
+ * Any output may be NULL.  Builds the plan's chunk table if needed
+ * (synchronises the device). */
 spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64_t *nnz,
                           int32_t *plan);
 
@@ -106,7 +108,11 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  *           through a two-stage shared-memory ring; 8 or 16: direct loads);
  * family 1: row-vector kernel, param = threads per row (1,2,4,8,16,32);
  * family 2: staged tile kernel, param = entries per thread segment (odd, 3..31);
- * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7, 11, 15.
+ * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7, 11, 15;
+ * family 4: slot-major warp-chunk kernel (values and column indices copied once
+ *           into chunk-major, lane-interleaved order and loaded coalesced into
+ *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 15);
+ *           the copy is built on first use and its values follow spmv_set_values.
  * param 0 keeps a default.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 

@@ -16,6 +16,7 @@
 #include "internal.h"
 #include "cg.h"
 #include "warp_kernel.cuh"
+#include "slot_kernel.cuh"
 
 namespace spmv {
 int64_t transpose_work_len(int32_t n_cols);
@@ -90,6 +91,17 @@ cudaError_t dmalloc(T **p, size_t count) {
     return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
 }
 
+// Slot-major copy of a matrix for plan family 4 (per entries-per-lane E).
+struct SlotTable {
+    ChunkDesc *d = nullptr;
+    uint32_t *lmask = nullptr;  // 32 words per chunk
+    void *vals = nullptr;       // n * 32E values, slot-major
+    int32_t *cols = nullptr;    // n * 32E column indices, slot-major
+    int32_t n = 0;
+    int32_t n_long = 0, n_empty = 0;
+    bool vals_valid = false;
+};
+
 struct ChunkTable {
     ChunkDesc *d = nullptr;
     uint32_t *masks = nullptr;
@@ -160,6 +172,48 @@ void free_chunks(ChunkTable &ct) {
     ct = ChunkTable();
 }
 
+// Chunks for the slot-major layout: the same row packing as make_chunks, from
+// the chunk's first entry itself (no alignment), with the row starts as one word
+// of E bits per lane.
+void make_slot_chunks(const int32_t *rp, int32_t n_rows, int E, std::vector<ChunkDesc> &out,
+                      std::vector<uint32_t> &lmask, int32_t *n_long, int32_t *n_empty) {
+    const int64_t SL = 32LL * E;
+    int32_t r = 0;
+    while (r < n_rows) {
+        const int32_t k0 = rp[r];
+        const size_t mo = lmask.size();
+        lmask.resize(mo + 32, 0u);
+        if (static_cast<int64_t>(rp[r + 1]) - k0 > SL) {
+            out.push_back(ChunkDesc{k0, rp[r + 1], r, (r + 1) | kChunkLong});
+            ++*n_long;
+            ++r;
+            continue;
+        }
+        bool empty = (rp[r + 1] == rp[r]);
+        int32_t r1 = r + 1;
+        while (r1 < n_rows && r1 - r < kWarpRowCap && static_cast<int64_t>(rp[r1 + 1]) - k0 <= SL) {
+            empty = empty || (rp[r1 + 1] == rp[r1]);
+            ++r1;
+        }
+        out.push_back(ChunkDesc{k0, rp[r1], r, r1 | (empty ? kChunkEmpty : 0)});
+        if (empty) ++*n_empty;
+        for (int32_t q = r; q < r1; ++q)
+            if (rp[q + 1] > rp[q]) {
+                const int32_t sl = rp[q] - k0;
+                lmask[mo + sl / E] |= 1u << (sl % E);
+            }
+        r = r1;
+    }
+}
+
+void free_slots(SlotTable &t) {
+    cudaFree(t.d);
+    cudaFree(t.lmask);
+    cudaFree(t.vals);
+    cudaFree(t.cols);
+    t = SlotTable();
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -211,6 +265,7 @@ struct spmv_matrix {
     std::map<std::pair<int, int>, TileTable> tables;  // (cap, rowcap) -> tiles
     std::map<int, ChunkTable> chunks;                   // E -> warp chunks
     std::map<int, ChunkTable> chunksT;                  // E -> warp chunks of A^T
+    std::map<int, SlotTable> slots;                     // E -> slot-major copy (family 4)
     int32_t *d_rmap = nullptr;                          // output row of each stored row
     // transposed structure (built on first use)
     bool has_T = false;
@@ -305,19 +360,17 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
     return best;
 }
 
-// Autotuner: from the row-length histogram choose the kernel and its work per
-// lane.  The pipelined warp-chunk kernel (family 0, odd E) keeps every FP64 FMA
-// lane busy whatever the row lengths, so it is the default.  Its entries per lane
-// E is 7 (chunks of 224 entries, 32 warps per SM) for mean row lengths below 20
-// and 15 (chunks of 480 entries, 16 warps per SM) above: short rows gain from
-// the extra warps in flight, long rows from fewer rows cut by lane boundaries
-// (measured on the 7-point, Hamiltonian-like and 27-point matrices).  The
-// row-vector kernel's lanes per row T (family 1) is the power of two nearest
-// half the mean row length, used when chosen explicitly.  FP32 storage halves
-// the bytes per chunk, so its chunks take 15 entries per lane unless the
-// columns are scattered, where 7 (more warps, more gathers in flight) wins
-// (measured: 7-point 68 vs 78 us, 27-point 117 vs 173 us, Hamiltonian-like
-// 165 vs 192 us).
+// Autotuner: from the row-length histogram and the column scatter choose the
+// kernel and its work per lane.  FP64: the slot-major chunk kernel (family 4)
+// with E = 7 entries per lane for mean row lengths below 10 and E = 9 above
+// (measured against the staged chunk kernels: Hamiltonian-like 150.6 vs
+// 196.6 us, 7-point 71.9 vs 74.3 us, 27-point 139.6 vs 159.2 us; E = 11, 13, 15
+// lose to 9 on all three).  FP32 storage: the slot-major kernel with E = 15 for
+// scattered columns (140.2 vs 152.1 us on the Hamiltonian-like matrix), the
+// two-stage staged kernel with E = 15 on stencils (56.2 vs 57.0 us on the
+// 7-point, 103.3 vs 103.6 us on the 27-point matrix).  The row-vector kernel's
+// lanes per row T (family 1) is the power of two nearest half the mean row
+// length, used when chosen explicitly.
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
     int T = 1;
@@ -325,16 +378,11 @@ void autotune(spmv_matrix *h) {
     h->T = T;
     const bool scattered = h->col_random > 0.25;
     if (h->vk == kF32) {
-        h->family = 0;
-        h->E = scattered ? 7 : 15;
-    } else if (scattered) {
-        // many columns far from those of the row before: the x gathers miss L1,
-        // so gather one chunk ahead (three-stage kernel)
-        h->family = 3;
+        h->family = scattered ? 4 : 0;
         h->E = 15;
     } else {
-        h->family = 0;
-        h->E = (mean < 20.0) ? 7 : 15;
+        h->family = 4;
+        h->E = (mean < 10.0) ? 7 : 9;
     }
 }
 
@@ -377,6 +425,42 @@ ChunkTable *get_chunks(spmv_matrix *h, int E, bool transposed) {
         return nullptr;
     }
     return &tabs.emplace(E, ct).first->second;
+}
+
+// The slot-major copy for E (built on first use; its values are laid out again
+// on the stream after spmv_set_values).
+SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s) {
+    auto it = h->slots.find(E);
+    if (it == h->slots.end()) {
+        std::vector<ChunkDesc> d;
+        std::vector<uint32_t> lm;
+        SlotTable t;
+        make_slot_chunks(h->h_rp.data(), h->n_rows, E, d, lm, &t.n_long, &t.n_empty);
+        t.n = static_cast<int32_t>(d.size());
+        const size_t nslots = static_cast<size_t>(t.n) * 32 * E;
+        const size_t vb = (h->vk == kF64) ? 8 : 4;
+        bool ok = dmalloc(&t.d, d.size()) == cudaSuccess && dmalloc(&t.lmask, lm.size()) == cudaSuccess &&
+                  cudaMalloc(&t.vals, nslots * vb + 16) == cudaSuccess && dmalloc(&t.cols, nslots + 4) == cudaSuccess;
+        ok = ok && (d.empty() || cudaMemcpy(t.d, d.data(), sizeof(ChunkDesc) * d.size(), cudaMemcpyHostToDevice) ==
+                                     cudaSuccess);
+        ok = ok && (lm.empty() || cudaMemcpy(t.lmask, lm.data(), 4 * lm.size(), cudaMemcpyHostToDevice) == cudaSuccess);
+        ok = ok && launch_slot_relayout(t.d, E, static_cast<int64_t>(nslots), h->vk, h->d_val, h->d_col, t.vals,
+                                        t.cols, s) == cudaSuccess;
+        if (!ok) {
+            free_slots(t);
+            return nullptr;
+        }
+        t.vals_valid = true;
+        it = h->slots.emplace(E, t).first;
+    }
+    SlotTable &t = it->second;
+    if (!t.vals_valid) {
+        if (launch_slot_relayout(t.d, E, static_cast<int64_t>(t.n) * 32 * E, h->vk, h->d_val, nullptr, t.vals,
+                                 nullptr, s) != cudaSuccess)
+            return nullptr;
+        t.vals_valid = true;
+    }
+    return &t;
 }
 
 void free_chunk_map(std::map<int, ChunkTable> &tabs) {
@@ -449,6 +533,7 @@ void destroy_matrix(spmv_matrix *h) {
     free_tables(h->tablesT);
     free_chunk_map(h->chunks);
     free_chunk_map(h->chunksT);
+    for (auto &kv : h->slots) free_slots(kv.second);
     cudaFree(h->d_rmap);
     destroy_cg(h->cg);
     if (h->mirror32) destroy_matrix(h->mirror32);
@@ -512,7 +597,25 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
                        int yk, cudaStream_t s) {
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-    if (h->family == 0 || h->family == 3 || h->d_rmap) {
+    SlotOps sops;
+    if (h->family == 4 && !h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, &sops)) {
+        SlotTable *t = get_slots(h, h->E, s);
+        if (!t) return SPMV_ERR_ALLOC;
+        SlotParams sp{};
+        sp.chunks = t->d;
+        sp.lmask = t->lmask;
+        sp.vals = t->vals;
+        sp.cols = t->cols;
+        sp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
+        sp.n_chunks = t->n;
+        sp.alpha = alpha;
+        sp.beta = beta;
+        return sops.launch(sp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+    }
+    // the staged chunk kernels (also family 4 in the vector and accumulator
+    // combinations the slot-major kernel is not compiled for: FP32 storage with
+    // an FP64 result or FP64 accumulation)
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
         int E = h->E;
         WarpOps ops;
         // family 3 selects the three-stage kernel of the same chunking (with the
@@ -646,7 +749,12 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 // allocation happens while a stream is being captured.
 static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-    if (h->family == 0 || h->family == 3 || h->d_rmap) {
+    SlotOps sops;
+    if (h->family == 4 && !h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, &sops)) {
+        if (!get_slots(h, h->E, nullptr)) return SPMV_ERR_ALLOC;
+        return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+    }
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
         int E = h->E;
         WarpOps ops;
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
@@ -737,6 +845,7 @@ spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *
     if (h->mirror32) CK(launch_convert(val, t, h->mirror32->d_val, kF32, h->nnz, s));
     h->valT_valid = false;
     h->valT_requested = false;
+    for (auto &kv : h->slots) kv.second.vals_valid = false;
     return SPMV_OK;
 }
 
@@ -762,6 +871,14 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
                 rowcap = c.rowcap;
                 threads = c.threads;
             }
+        } else if (h->family == 4) {
+            SlotTable *t = get_slots(h, E, nullptr);
+            if (t) {
+                nunits = t->n;
+                nlong = t->n_long;
+            }
+            rowcap = kWarpRowCap;
+            if (cudaDeviceSynchronize() != cudaSuccess) return SPMV_ERR_CUDA;
         } else {
             WarpOps ops;
             const bool ok3 = h->family == 3 && warp_ops(h->vk, h->vk, h->vk, acc, E + 100, false, false, &ops);
@@ -796,7 +913,14 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 }
 
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
-    if (!h || family < 0 || family > 3) return SPMV_ERR_INVALID_ARG;
+    if (!h || family < 0 || family > 4) return SPMV_ERR_INVALID_ARG;
+    if (family == 4) {
+        if (param != 0 && param != 7 && param != 9 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
+        if (h->vk == kF32 && (param == 9 || param == 11)) return SPMV_ERR_INVALID_ARG;
+        h->family = 4;
+        h->E = param ? param : (h->vk == kF32 ? 15 : 9);
+        return SPMV_OK;
+    }
     if (family == 3) {
         if (param != 0 && param != 7 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
         h->family = 3;

@@ -84,10 +84,20 @@ bool warp_ops(int vk, int xk, int yk, int acc, int E, bool indirect, bool batche
 bool warp_ops_f64(int E, bool indirect, bool batched, WarpOps *ops);
 bool warp_ops_f32(int yk, int acc, int E, bool indirect, bool batched, WarpOps *ops);
 
+struct SlotParams;
+// One compiled configuration of the slot-major chunk kernel (plan family 4).
+struct SlotOps {
+    cudaError_t (*launch)(const SlotParams &, cudaStream_t);
+};
+bool slot_ops(int vk, int xk, int yk, int acc, int E, SlotOps *ops);
+// Slot-major copies of the values (and, when cols_out is not null, the column
+// indices) of the regular chunks in `chunks` (ChunkDesc[n_slots / (32E)]).
+cudaError_t launch_slot_relayout(const void *chunks, int E, int64_t n_slots, int vk, const void *val,
+                                 const int32_t *col, void *vals_out, int32_t *cols_out, cudaStream_t s);
+
 cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
                           int T, cudaStream_t s);
 
-// Halo gather: halo[h] = x[map[h]].
 // out[k] = val[perm[k]] for k < nnz (values of kind vk: FP64 or FP32).
 cudaError_t launch_permute(const void *val, const int32_t *perm, void *out, int64_t nnz, int vk, cudaStream_t s);
 // Device-side CRS check; sets *bad to 1 on any violation.
@@ -96,6 +106,7 @@ cudaError_t launch_validate(int32_t n_rows, int32_t n_cols, int64_t nnz, const i
 // One warp waits on an mbarrier nothing completes, for limit_ns, then records
 // kDevErrTimeout in *err.
 cudaError_t launch_wait_timeout(uint64_t limit_ns, int32_t *err, cudaStream_t s);
+// Halo gather: halo[h] = x[map[h]].
 cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int64_t n,
                           cudaStream_t s);
 

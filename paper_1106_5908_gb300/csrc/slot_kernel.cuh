@@ -1,0 +1,212 @@
+// Slot-major warp-chunk kernel (plan family 4).
+//
+// Same chunking (whole rows, at most 32*E entries and kWarpRowCap rows per
+// chunk), row-start bits, per-lane FMA chains and lane-order carries as the
+// staged chunk kernels, with a different home for the streamed operands: the
+// values and column indices of each regular chunk are stored once in slot-major
+// order, entry k0 + l*E + e of the chunk at [chunk][e][l].  The e-th load of a
+// warp therefore reads 32 consecutive elements (one coalesced access), nothing
+// is staged in shared memory, and the streamed loads bypass L1 (evict-first in
+// L2), which leaves the whole L1 to the x gathers.  A warp keeps the next
+// chunk's gathers and values and the chunk after's column indices in flight in
+// registers while its FMA chains run.
+#pragma once
+#include "warp_kernel.cuh"
+
+namespace spmv {
+
+struct SlotParams {
+    const ChunkDesc *chunks;
+    const uint32_t *lmask;  // 32 words per chunk: bit e of word l = a row starts at slot l*E + e
+    const void *vals;       // n_chunks * 32E values, slot-major (zero in padding)
+    const int32_t *cols;    // n_chunks * 32E column indices, slot-major (zero in padding)
+    MatRef m;               // the CRS itself (long and empty-row chunks), x, y, row map
+    int32_t n_chunks;
+    double alpha, beta;
+};
+
+__device__ __forceinline__ double ld_stream(const double *p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
+    constexpr int SL = 32 * E;
+    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
+    __shared__ ACC s_rows[8][kWarpRowCap];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * 8;
+    const int n = p.n_chunks;
+    int c = blockIdx.x * 8 + wib;
+    if (c >= n) return;
+    ACC *srow = s_rows[wib];
+    const uint64_t pol = l2_evict_first_policy();
+    const VT *__restrict__ vals = static_cast<const VT *>(p.vals);
+    const XT *__restrict__ x = static_cast<const XT *>(p.m.x);
+    YT *__restrict__ y = static_cast<YT *>(p.m.y);
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+
+    auto regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
+    auto hi_of = [&](const ChunkDesc &d) { return max(0, min(E, d.k1 - d.k0 - lane * E)); };
+    auto load_cols = [&](int cc, int32_t (&cl)[E]) {
+        const int32_t *b = p.cols + static_cast<int64_t>(cc) * SL + lane;
+#pragma unroll
+        for (int e = 0; e < E; ++e) cl[e] = ld_stream(b + e * 32, pol);
+    };
+    auto load_vals = [&](int cc, VT (&v)[E]) {
+        const VT *b = vals + static_cast<int64_t>(cc) * SL + lane;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = ld_stream(b + e * 32, pol);
+    };
+    auto gather = [&](const ChunkDesc &d, const int32_t (&cl)[E], XT (&xv)[E]) {
+        const int hi = regular(d) ? hi_of(d) : 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) xv[e] = (e < hi) ? __ldg(x + cl[e]) : XT(0);
+    };
+    auto load_desc = [&](int cc) {
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(p.chunks) + cc);
+        return ChunkDesc{q.x, q.y, q.z, q.w};
+    };
+
+    // chunk c: descriptor, row starts, gathers, values; chunk c + nwarps:
+    // descriptor, row starts, column indices
+    ChunkDesc dc = load_desc(c);
+    uint32_t mc = __ldg(p.lmask + static_cast<int64_t>(c) * 32 + lane);
+    XT xc[E];
+    VT vc[E];
+    {
+        int32_t cl[E];
+        load_cols(c, cl);
+        gather(dc, cl, xc);
+        load_vals(c, vc);
+    }
+    ChunkDesc dn{};
+    uint32_t mn = 0;
+    int32_t cn[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) cn[e] = 0;
+    if (c + nwarps < n) {
+        dn = load_desc(c + nwarps);
+        mn = __ldg(p.lmask + static_cast<int64_t>(c + nwarps) * 32 + lane);
+        load_cols(c + nwarps, cn);
+    }
+
+    for (; c < n; c += nwarps) {
+        const int c1 = c + nwarps, c2 = c + 2 * nwarps;
+        // chunk c1: gathers and values; chunk c2: descriptor, row starts, columns
+        XT xn[E];
+        VT vn[E];
+        if (c1 < n) {
+            gather(dn, cn, xn);
+            load_vals(c1, vn);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                xn[e] = XT(0);
+                vn[e] = VT(0);
+            }
+        }
+        ChunkDesc d2{};
+        uint32_t m2 = 0;
+        int32_t c2l[E];
+        if (c2 < n) {
+            d2 = load_desc(c2);
+            m2 = __ldg(p.lmask + static_cast<int64_t>(c2) * 32 + lane);
+            load_cols(c2, c2l);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) c2l[e] = 0;
+        }
+        // ---- chunk c ---------------------------------------------------------
+        const int r0 = dc.r0;
+        const int r1 = dc.r1f & kChunkRowMask;
+        if (dc.r1f & kChunkLong) {
+            long_row<VT, XT, YT, ACC, false>(p.m, dc, x, y, alpha, beta, plain, lane);
+        } else if (dc.r1f & kChunkEmpty) {
+            rows_per_lane<VT, XT, YT, ACC, false>(p.m, r0, r1, x, y, alpha, beta, plain, lane);
+        } else {
+            const int hi = hi_of(dc);
+            const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mc, 1);
+            const bool ends = (lane * E + E >= dc.k1 - dc.k0) || (lane < 31 && (next_bits & 1u));
+            chunk_lane<E, VT, XT, ACC>(vc, xc, mc, 0, hi, ends, r0, srow, lane);
+            __syncwarp();
+            for (int q = lane; q < r1 - r0; q += 32) store_acc(y, r0 + q, srow[q], alpha, beta, plain, p.m.rmap);
+        }
+        __syncwarp();  // the row buffer is free again
+        dc = dn;
+        mc = mn;
+        dn = d2;
+        mn = m2;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            xc[e] = xn[e];
+            vc[e] = vn[e];
+            cn[e] = c2l[e];
+        }
+    }
+}
+
+// Slot-major copies of a CRS: slot t = chunk*32E + e*32 + l holds entry
+// k0 + l*E + e of the chunk when the chunk is regular and the entry belongs to
+// it, else zero.  cols_out may be null (values only, after new values).
+template <typename VT>
+__global__ void __launch_bounds__(256) k_slot_relayout(const ChunkDesc *__restrict__ chunks, int E,
+                                                       int64_t n_slots, const VT *__restrict__ val,
+                                                       const int32_t *__restrict__ col, VT *__restrict__ vals_out,
+                                                       int32_t *__restrict__ cols_out) {
+    const int64_t SL = 32LL * E;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_slots; t += stride) {
+        const int64_t cc = t / SL;
+        const int r = static_cast<int>(t - cc * SL);
+        const int e = r >> 5, l = r & 31;
+        const ChunkDesc d = chunks[cc];
+        const int64_t k = static_cast<int64_t>(d.k0) + static_cast<int64_t>(l) * E + e;
+        const bool ok = ((d.r1f & (kChunkLong | kChunkEmpty)) == 0) && k < d.k1;
+        vals_out[t] = ok ? val[k] : VT(0);
+        if (cols_out) cols_out[t] = ok ? col[k] : 0;
+    }
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC>
+struct SlotKernel {
+    static int grid_limit() {
+        static int cached = -1;
+        static int cached_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cached >= 0 && cached_dev == dev) return cached;
+        int per_sm = 0, sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot<E, VT, XT, YT, ACC>, 256, 0) !=
+            cudaSuccess)
+            return 0;
+        cached = per_sm * sms;
+        cached_dev = dev;
+        return cached;
+    }
+    static cudaError_t launch(const SlotParams &p, cudaStream_t s) {
+        if (p.n_chunks <= 0) return cudaSuccess;
+        const int lim = grid_limit();
+        if (lim <= 0) return cudaErrorInvalidConfiguration;
+        const int want = (p.n_chunks + 7) / 8;
+        k_slot<E, VT, XT, YT, ACC><<<want < lim ? want : lim, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace spmv

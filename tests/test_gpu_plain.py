@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (0, 16), (0, 8), (2, 7), (2, 15),
+         (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
 
 
 def make(A, dtype=None):
@@ -40,7 +41,7 @@ def test_random_plans(shape, plan):
         assert_within(host(y), ref, bound, 1e-13, f"plan {plan} a={alpha} b={beta}")
 
 
-@pytest.mark.parametrize("plan", PLANS[:9])
+@pytest.mark.parametrize("plan", PLANS[:13])
 @pytest.mark.parametrize("long_len", [253, 257, 509, 513, 1791, 1793, 3841, 9000, 40000])
 def test_long_rows(plan, long_len):
     """Rows longer than a tile take the CTA-wide path; mixed with short ones."""
@@ -55,6 +56,9 @@ def test_long_rows(plan, long_len):
     if plan[0] == 2:
         cap = {7: 1792, 15: 3840, 31: 7936}[plan[1]]
         assert info["long_rows"] == int((np.diff(A.row_ptr) > cap).sum())
+    elif plan[0] == 4:
+        # slot-major chunks start at the row's first entry
+        assert info["long_rows"] == int((np.diff(A.row_ptr) > 32 * plan[1]).sum())
     else:
         # a row is long when it does not fit 32*E slots from the aligned start
         slots = 32 * plan[1]
@@ -185,21 +189,17 @@ def test_laplace3d_160_fp32(c3):
 
 
 def test_autotuner_choices():
-    """The tuner picks the three-stage chunk kernel for scattered columns and the
-    two-stage one for stencils, with entries per lane from the mean row length
-    (FP64), or from the column scatter (FP32 storage)."""
+    """The tuner picks the slot-major chunk kernel for FP64, with 7 entries per
+    lane for short rows and 9 otherwise; for FP32 storage the slot-major kernel
+    when the columns are scattered and the staged two-stage kernel on stencils."""
     from paper_1106_5908_gb300 import Matrix
     H = W.hamiltonian_like(50000, seed=3)
-    info = Matrix.from_csr(H.row_ptr, H.col_idx, H.val, H.n_cols).info()
-    assert (info["family"], info["E"]) == (3, 15)
     L3 = W.laplace3d(24)
-    info = Matrix.from_csr(L3.row_ptr, L3.col_idx, L3.val, L3.n_cols).info()
-    assert (info["family"], info["E"]) == (0, 7)
     S27 = W.stencil27(20, seed=1)
-    info = Matrix.from_csr(S27.row_ptr, S27.col_idx, S27.val, S27.n_cols).info()
-    assert (info["family"], info["E"]) == (0, 15)
-    # FP32 storage: 15 entries per lane unless the columns are scattered
-    for A, want in ((H, (0, 7)), (L3, (0, 15)), (S27, (0, 15))):
+    for A, want in ((H, (4, 9)), (L3, (4, 7)), (S27, (4, 9))):
+        info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols).info()
+        assert (info["family"], info["E"]) == want
+    for A, want in ((H, (4, 15)), (L3, (0, 15)), (S27, (0, 15))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
         assert (info["family"], info["E"]) == want
 
@@ -229,3 +229,25 @@ def test_fp32_widening_exact(acc, plan):
     nan = np.isnan(want)
     assert np.array_equal(np.isnan(y), nan)
     assert np.array_equal(y[~nan], want[~nan]), np.flatnonzero(y[~nan] != want[~nan])[:8]
+
+
+@pytest.mark.parametrize("plan", [(4, 7), (4, 15)])
+def test_slot_major_follows_new_values(plan):
+    """The slot-major copy (plan family 4) is laid out again after new values, in
+    FP64 and in FP32 storage."""
+    A = W.random_csr(5000, 4000, seed=41, max_len=40, long_rows=2, long_len=3000)
+    x = W.uniform(A.n_cols, 1)
+    for dt in (None, torch.float32):
+        M = make(A, dtype=dt)
+        M.set_plan(*plan)
+        M.apply(dev(x if dt is None else x.astype(np.float32)))
+        v2 = W.uniform(A.nnz, 2)
+        M.set_values(dev(v2) if dt is None else dev(v2.astype(np.float32)))
+        if dt is None:
+            ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v2, x, with_bound=True)
+            assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, f"slot-major f64 {plan}")
+        else:
+            v32 = v2.astype(np.float32).astype(np.float64)
+            x32 = x.astype(np.float32)
+            ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32, x32.astype(np.float64), with_bound=True)
+            assert_within(host(M.apply(dev(x32))), ref, bound, 1e-6, f"slot-major f32 {plan}")
