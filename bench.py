@@ -39,8 +39,8 @@ UNIT = "GB/s"
 # DRAM traffic of one launch of the plain FP64 chunk kernel on this workload, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_hash": "03c82c1b5b9f0b53", "bytes_per_launch": 708644011,
-           "source": "profiles/k_pipe3_f64_hamiltonian_c2.md (mean of 3 launches)"}
+TRAFFIC = {"kernel_hash": "2d6a1c6c64a0af95", "bytes_per_launch": 751312725,
+           "source": "profiles/k_slot_f64_hamiltonian_c2.md (mean of 3 launches)"}
 
 
 def kernel_hash() -> str:
