@@ -598,7 +598,8 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     SlotOps sops;
-    if (h->family == 4 && !h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, &sops)) {
+    if (h->family == 4 && ((h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, true, &sops)) ||
+                           slot_ops(h->vk, xk, yk, acc, h->E, false, &sops))) {
         SlotTable *t = get_slots(h, h->E, s);
         if (!t) return SPMV_ERR_ALLOC;
         SlotParams sp{};
@@ -606,7 +607,7 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
         sp.lmask = t->lmask;
         sp.vals = t->vals;
         sp.cols = t->cols;
-        sp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
+        sp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, h->d_rmap};
         sp.n_chunks = t->n;
         sp.alpha = alpha;
         sp.beta = beta;
@@ -750,7 +751,7 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     SlotOps sops;
-    if (h->family == 4 && !h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, &sops)) {
+    if (h->family == 4 && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops)) {
         if (!get_slots(h, h->E, nullptr)) return SPMV_ERR_ALLOC;
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     }
@@ -1101,18 +1102,17 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
         return st;
     }
     // Plans of the parts (measured on the Hamiltonian-like matrix, 8 blocks): the
-    // local part keeps mostly near columns, whose gathers hit L1, so it runs on
-    // the two-stage kernel (294 vs 311 us for the whole split product); the
-    // nonlocal part's gathers go to the halo buffer, so it gathers one chunk
-    // ahead with 15 entries per lane (three-stage kernel, row epilogue loaded
-    // ahead).
+    // local part takes the autotuned plan (slot-major); the nonlocal part runs
+    // the slot-major kernel with 7 entries per lane and its row epilogue (row
+    // map, old y) loaded ahead of the FMA chains (split 283 -> 267 us against the
+    // staged three-stage kernel).
     if (sp->Aloc->family == 3) {
         const double mean = n ? static_cast<double>(sp->Aloc->nnz) / n : 0.0;
         sp->Aloc->family = 0;
         sp->Aloc->E = (mean < 20.0) ? 7 : 15;
     }
-    sp->Anl->family = 3;
-    sp->Anl->E = 15;
+    sp->Anl->family = 4;
+    sp->Anl->E = 7;
     if (halo_count_out)
         for (int b = 0; b < nblocks; ++b) halo_count_out[b] = sp->halo_count[b];
     *out = sp;

@@ -5,7 +5,15 @@
 
 namespace spmv {
 
-bool slot_ops(int vk, int xk, int yk, int acc, int E, SlotOps *ops) {
+bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
+    if (pre) {
+        // row-mapped products (the split's nonlocal part): FP64, E = 7
+        if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64 && E == 7) {
+            ops->launch = &SlotKernel<7, double, double, double, AccF64, true>::launch;
+            return true;
+        }
+        return false;
+    }
 #define SPMV_S(VK_, XK_, YK_, ACCK_, E_, VT_, XT_, YT_, ACC_)                                 \
     if (vk == VK_ && xk == XK_ && yk == YK_ && acc == ACCK_ && E == E_) {                     \
         ops->launch = &SlotKernel<E_, VT_, XT_, YT_, ACC_>::launch;                            \

@@ -41,7 +41,9 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
     return v;
 }
 
-template <int E, typename VT, typename XT, typename YT, typename ACC>
+// PRE: the row epilogue's operands (row map, old y) are loaded before the FMA
+// chains (row-mapped products: the nonlocal part of the split form).
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false>
 __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
     constexpr int SL = 32 * E;
     static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
@@ -139,12 +141,19 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         } else if (dc.r1f & kChunkEmpty) {
             rows_per_lane<VT, XT, YT, ACC, false>(p.m, r0, r1, x, y, alpha, beta, plain, lane);
         } else {
+            RowEpilogue<YT> epi;
+            if constexpr (PRE) epi.prefetch(y, p.m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
             const int hi = hi_of(dc);
             const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mc, 1);
             const bool ends = (lane * E + E >= dc.k1 - dc.k0) || (lane < 31 && (next_bits & 1u));
             chunk_lane<E, VT, XT, ACC>(vc, xc, mc, 0, hi, ends, r0, srow, lane);
             __syncwarp();
-            for (int q = lane; q < r1 - r0; q += 32) store_acc(y, r0 + q, srow[q], alpha, beta, plain, p.m.rmap);
+            if constexpr (PRE) {
+                epi.store(y, srow, r1 - r0, alpha, beta, plain, lane);
+            } else {
+                for (int q = lane; q < r1 - r0; q += 32)
+                    store_acc(y, r0 + q, srow[q], alpha, beta, plain, p.m.rmap);
+            }
         }
         __syncwarp();  // the row buffer is free again
         dc = dn;
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__(256) k_slot_relayout(const ChunkDesc *__restri
     }
 }
 
-template <int E, typename VT, typename XT, typename YT, typename ACC>
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false>
 struct SlotKernel {
     static int grid_limit() {
         static int cached = -1;
@@ -192,7 +201,7 @@ struct SlotKernel {
         if (cached >= 0 && cached_dev == dev) return cached;
         int per_sm = 0, sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot<E, VT, XT, YT, ACC>, 256, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot<E, VT, XT, YT, ACC, PRE>, 256, 0) !=
             cudaSuccess)
             return 0;
         cached = per_sm * sms;
@@ -204,7 +213,7 @@ struct SlotKernel {
         const int lim = grid_limit();
         if (lim <= 0) return cudaErrorInvalidConfiguration;
         const int want = (p.n_chunks + 7) / 8;
-        k_slot<E, VT, XT, YT, ACC><<<want < lim ? want : lim, 256, 0, s>>>(p);
+        k_slot<E, VT, XT, YT, ACC, PRE><<<want < lim ? want : lim, 256, 0, s>>>(p);
         return cudaGetLastError();
     }
 };
