@@ -173,8 +173,9 @@ void free_chunks(ChunkTable &ct) {
 }
 
 // Chunks for the slot-major layout: the same row packing as make_chunks, from
-// the chunk's first entry itself (no alignment), with the row starts as one word
-// of E bits per lane.
+// the chunk's first entry itself (no alignment), with one word per lane: the row
+// starts in its E slots (bits 0..E-1), the rows starting before them (bits
+// kSlotPreShift..) and whether its last slot ends a row or the chunk (kSlotEnds).
 void make_slot_chunks(const int32_t *rp, int32_t n_rows, int E, std::vector<ChunkDesc> &out,
                       std::vector<uint32_t> &lmask, int32_t *n_long, int32_t *n_empty) {
     const int64_t SL = 32LL * E;
@@ -202,6 +203,17 @@ void make_slot_chunks(const int32_t *rp, int32_t n_rows, int E, std::vector<Chun
                 const int32_t sl = rp[q] - k0;
                 lmask[mo + sl / E] |= 1u << (sl % E);
             }
+        if (!empty) {
+            const int64_t n_used = static_cast<int64_t>(rp[r1]) - k0;
+            uint32_t pre = 0;
+            for (int lane = 0; lane < 32; ++lane) {
+                const uint32_t bits = lmask[mo + lane];
+                const bool ends = static_cast<int64_t>(lane + 1) * E >= n_used ||
+                                  (lane < 31 && (lmask[mo + lane + 1] & 1u));
+                lmask[mo + lane] = bits | (pre << kSlotPreShift) | (ends ? kSlotEnds : 0u);
+                pre += static_cast<uint32_t>(__builtin_popcount(bits));
+            }
+        }
         r = r1;
     }
 }

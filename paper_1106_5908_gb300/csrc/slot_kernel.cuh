@@ -15,9 +15,18 @@
 
 namespace spmv {
 
+// Lane word of a regular chunk: bit e (e < E <= 15) = a row starts at slot
+// l*E + e; bits 16-22 = rows starting in the chunk before the lane's slots; bit
+// 23 = the lane's last slot ends a row or the chunk.  All follow from the row
+// starts, so they are set once on the host and the kernel needs no cross-lane
+// scan for them.
+constexpr int kSlotPreShift = 16;
+constexpr uint32_t kSlotPreMask = 0x7fu;
+constexpr uint32_t kSlotEnds = 1u << 23;
+
 struct SlotParams {
     const ChunkDesc *chunks;
-    const uint32_t *lmask;  // 32 words per chunk: bit e of word l = a row starts at slot l*E + e
+    const uint32_t *lmask;  // 32 words per chunk (kSlotPre*, kSlotEnds below)
     const void *vals;       // n_chunks * 32E values, slot-major (zero in padding)
     const int32_t *cols;    // n_chunks * 32E column indices, slot-major (zero in padding)
     MatRef m;               // the CRS itself (long and empty-row chunks), x, y, row map
@@ -40,6 +49,15 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
+
+// Whether a configuration takes the lanes' row counts from a shuffle scan
+// instead of the packed lane words: only FP64 with E = 9 (150.1 against
+// 152.5 us on the Hamiltonian-like matrix; the packed words win elsewhere, e.g.
+// E = 11 154 against 169 us, the split's nonlocal part 256 against 262 us).
+template <int E, typename VT, bool PRE>
+struct kSlotScan {
+    static constexpr bool value = std::is_same<VT, double>::value && E == 9 && !PRE;
+};
 
 // PRE: the row epilogue's operands (row map, old y) are loaded before the FMA
 // chains (row-mapped products: the nonlocal part of the split form).
@@ -144,9 +162,16 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
             RowEpilogue<YT> epi;
             if constexpr (PRE) epi.prefetch(y, p.m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
             const int hi = hi_of(dc);
-            const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mc, 1);
-            const bool ends = (lane * E + E >= dc.k1 - dc.k0) || (lane < 31 && (next_bits & 1u));
-            chunk_lane<E, VT, XT, ACC>(vc, xc, mc, 0, hi, ends, r0, srow, lane);
+            const uint32_t mbits = mc & ((1u << E) - 1u);
+            if constexpr (kSlotScan<E, VT, PRE>::value) {
+                const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
+                const bool ends = (lane * E + E >= dc.k1 - dc.k0) || (lane < 31 && (next_bits & 1u));
+                chunk_lane<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, ends, r0, srow, lane);
+            } else {
+                chunk_lane_pre<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, (mc & kSlotEnds) != 0u,
+                                               static_cast<int>((mc >> kSlotPreShift) & kSlotPreMask), r0,
+                                               srow, lane);
+            }
             __syncwarp();
             if constexpr (PRE) {
                 epi.store(y, srow, r1 - r0, alpha, beta, plain, lane);

@@ -218,17 +218,11 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
 // is known to have started in this lane, so the last store of a row is its full
 // sum.  The part of the first row that started in an earlier lane is combined in
 // lane order with the carries of those lanes (one FP64 add per crossing).
+// `pre` is the number of rows starting in the chunk before this lane's slots.
 template <int E, typename VT, typename XT, typename ACC>
-__device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
-                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
-    const int cnt = __popc(mbits);
-    int pre = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += t;
-    }
-    pre -= cnt;  // row starts in the chunk before this lane's slots
+__device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
+                                               int lo, int hi, bool ends, int pre, int r0, ACC *srow,
+                                               int lane) {
     const bool active = lo < hi;
     const bool starts_first = active && ((mbits >> lo) & 1u);
     int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
@@ -273,6 +267,21 @@ __device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E
         ++dist;
     }
     if (has_pend) srow[first_row - r0] = tot;
+}
+
+// As chunk_lane_pre, with `pre` from a shuffle scan of the lanes' row-start counts.
+template <int E, typename VT, typename XT, typename ACC>
+__device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
+                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
+    const int cnt = __popc(mbits);
+    int pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += t;
+    }
+    pre -= cnt;
+    chunk_lane_pre<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, pre, r0, srow, lane);
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
