@@ -278,6 +278,7 @@ struct spmv_matrix {
     std::map<int, ChunkTable> chunks;                   // E -> warp chunks
     std::map<int, ChunkTable> chunksT;                  // E -> warp chunks of A^T
     std::map<int, SlotTable> slots;                     // E -> slot-major copy (family 4)
+    std::map<int, SlotTable> slotsT;                    // E -> slot-major copy of A^T (reverse pass)
     int32_t *d_rmap = nullptr;                          // output row of each stored row
     // transposed structure (built on first use)
     bool has_T = false;
@@ -440,14 +441,21 @@ ChunkTable *get_chunks(spmv_matrix *h, int E, bool transposed) {
 }
 
 // The slot-major copy for E (built on first use; its values are laid out again
-// on the stream after spmv_set_values).
-SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s) {
-    auto it = h->slots.find(E);
-    if (it == h->slots.end()) {
+// on the stream after spmv_set_values).  transposed: the copy of A^T, from the
+// transposed structure and the values laid out in A^T order (d_valT).
+SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s, bool transposed = false) {
+    auto &tabs = transposed ? h->slotsT : h->slots;
+    const int32_t *d_col = transposed ? h->d_colT : h->d_col;
+    const void *d_val = transposed ? h->d_valT : h->d_val;
+    auto it = tabs.find(E);
+    if (it == tabs.end()) {
         std::vector<ChunkDesc> d;
         std::vector<uint32_t> lm;
         SlotTable t;
-        make_slot_chunks(h->h_rp.data(), h->n_rows, E, d, lm, &t.n_long, &t.n_empty);
+        if (transposed)
+            make_slot_chunks(h->h_rowT.data(), h->n_cols, E, d, lm, &t.n_long, &t.n_empty);
+        else
+            make_slot_chunks(h->h_rp.data(), h->n_rows, E, d, lm, &t.n_long, &t.n_empty);
         t.n = static_cast<int32_t>(d.size());
         const size_t nslots = static_cast<size_t>(t.n) * 32 * E;
         const size_t vb = (h->vk == kF64) ? 8 : 4;
@@ -456,18 +464,18 @@ SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s) {
         ok = ok && (d.empty() || cudaMemcpy(t.d, d.data(), sizeof(ChunkDesc) * d.size(), cudaMemcpyHostToDevice) ==
                                      cudaSuccess);
         ok = ok && (lm.empty() || cudaMemcpy(t.lmask, lm.data(), 4 * lm.size(), cudaMemcpyHostToDevice) == cudaSuccess);
-        ok = ok && launch_slot_relayout(t.d, E, static_cast<int64_t>(nslots), h->vk, h->d_val, h->d_col, t.vals,
-                                        t.cols, s) == cudaSuccess;
+        ok = ok && launch_slot_relayout(t.d, E, static_cast<int64_t>(nslots), h->vk, d_val, d_col, t.vals, t.cols,
+                                        s) == cudaSuccess;
         if (!ok) {
             free_slots(t);
             return nullptr;
         }
         t.vals_valid = true;
-        it = h->slots.emplace(E, t).first;
+        it = tabs.emplace(E, t).first;
     }
     SlotTable &t = it->second;
     if (!t.vals_valid) {
-        if (launch_slot_relayout(t.d, E, static_cast<int64_t>(t.n) * 32 * E, h->vk, h->d_val, nullptr, t.vals,
+        if (launch_slot_relayout(t.d, E, static_cast<int64_t>(t.n) * 32 * E, h->vk, d_val, nullptr, t.vals,
                                  nullptr, s) != cudaSuccess)
             return nullptr;
         t.vals_valid = true;
@@ -546,6 +554,7 @@ void destroy_matrix(spmv_matrix *h) {
     free_chunk_map(h->chunks);
     free_chunk_map(h->chunksT);
     for (auto &kv : h->slots) free_slots(kv.second);
+    for (auto &kv : h->slotsT) free_slots(kv.second);
     cudaFree(h->d_rmap);
     destroy_cg(h->cg);
     if (h->mirror32) destroy_matrix(h->mirror32);
@@ -1262,9 +1271,10 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         if (st != SPMV_OK) return st;
         // grad_x = alpha * A^T g: warp chunks over the rows of A^T.  The first
         // reverse pass on a set of values reads them through the permutation
-        // (val[perm], inside the kernel); a second one on the same values lays
-        // them out in the order of A^T once (a streaming permutation pass), and
-        // from then on the product streams them like a forward product.
+        // (val[perm], inside the staged chunk kernel); a second one on the same
+        // values lays them out in the order of A^T once (a streaming permutation
+        // pass), and from then on the product runs like a forward product on a
+        // slot-major copy of A^T.
         const size_t vb = (h->vk == kF64) ? 8 : 4;
         if (!h->valT_valid && h->valT_requested && h->nnz > 0) {
             if (!h->d_valT && cudaMalloc(&h->d_valT, static_cast<size_t>(h->nnz) * vb) != cudaSuccess) {
@@ -1273,27 +1283,54 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
             }
             CK(launch_permute(h->d_val, h->d_perm, h->d_valT, h->nnz, h->vk, s));
             h->valT_valid = true;
+            for (auto &kv : h->slotsT) kv.second.vals_valid = false;
         }
         const bool ind = !h->valT_valid;
         h->valT_requested = true;
-        WarpOps ops;
-        const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
-        const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
-        int ET = (meanT < 20.0) ? 7 : 15;
-        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) ET = 15;
-        if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) return SPMV_ERR_UNSUPPORTED;
-        ChunkTable *ct = get_chunks(h, ET, true);
-        if (!ct) return SPMV_ERR_ALLOC;
-        WarpParams wp{};
-        wp.m = ind ? MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr}
-                   : MatRef{h->d_rowT, h->d_colT, h->d_valT, nullptr, g, grad_x, nullptr};
-        wp.chunks = ct->d;
-        wp.masks = ct->masks;
-        wp.n_chunks = ct->n;
-        wp.alpha = alpha;
-        wp.beta = 0.0;
-        wp.err = h->d_err;
-        if (ops.launch(wp, ct->n, s) != cudaSuccess) return SPMV_ERR_CUDA;
+        bool done = false;
+        if (!ind) {
+            // A^T's values in its own order: the slot-major kernel on a slot-major
+            // copy of A^T (E by A^T's mean row length, as for a forward product)
+            const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
+            const int ES = (h->vk == kF32) ? 15 : ((meanT < 10.0) ? 7 : 9);
+            SlotOps sops;
+            const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
+            if (slot_ops(h->vk, h->vk, h->vk, acc, ES, false, &sops)) {
+                SlotTable *t = get_slots(h, ES, s, true);
+                if (!t) return SPMV_ERR_ALLOC;
+                SlotParams sp{};
+                sp.chunks = t->d;
+                sp.lmask = t->lmask;
+                sp.vals = t->vals;
+                sp.cols = t->cols;
+                sp.m = MatRef{h->d_rowT, h->d_colT, h->d_valT, nullptr, g, grad_x, nullptr};
+                sp.n_chunks = t->n;
+                sp.alpha = alpha;
+                sp.beta = 0.0;
+                if (sops.launch(sp, s) != cudaSuccess) return SPMV_ERR_CUDA;
+                done = true;
+            }
+        }
+        if (!done) {
+            WarpOps ops;
+            const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
+            const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
+            int ET = (meanT < 20.0) ? 7 : 15;
+            if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) ET = 15;
+            if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+            ChunkTable *ct = get_chunks(h, ET, true);
+            if (!ct) return SPMV_ERR_ALLOC;
+            WarpParams wp{};
+            wp.m = ind ? MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, g, grad_x, nullptr}
+                       : MatRef{h->d_rowT, h->d_colT, h->d_valT, nullptr, g, grad_x, nullptr};
+            wp.chunks = ct->d;
+            wp.masks = ct->masks;
+            wp.n_chunks = ct->n;
+            wp.alpha = alpha;
+            wp.beta = 0.0;
+            wp.err = h->d_err;
+            if (ops.launch(wp, ct->n, s) != cudaSuccess) return SPMV_ERR_CUDA;
+        }
     }
     if (grad_val && h->nnz > 0) {
         // the forward plan's chunks (any E): rows from the row-start bitmasks
