@@ -250,10 +250,12 @@ spmv_status spmv_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
 /* ------------------------------------------------------------------------ */
 
 /* Group count matrix handles (all FP64 or all FP32 storage) into one batch whose
- * apply is a single persistent kernel launch over the tiles of every matrix,
- * captured once into a CUDA graph and replayed.  The per-thread work E and the
- * tile size come from the combined row-length histogram.  The handles must
- * outlive the batch. */
+ * apply is a single persistent kernel launch over the warp chunks of every
+ * matrix (the slot-major chunk kernel on one concatenated slot-major copy of all
+ * matrices, 7 entries per lane), captured once into a CUDA graph and replayed.
+ * The batch holds its own copy of the values: after spmv_set_values on a member,
+ * the next spmv_batched_apply lays that member's values out again (on stream,
+ * before the launch).  The handles must outlive the batch. */
 spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spmv_handle *mats);
 void spmv_batched_destroy(spmv_batch_handle b);
 
@@ -265,7 +267,8 @@ void spmv_batched_destroy(spmv_batch_handle b);
 spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *const *x,
                                double beta, void *const *y, void *stream);
 
-/* plan[0..3]: E, threads per CTA, total tiles, persistent grid size. */
+/* plan[0..3]: E, threads per CTA, total chunks, persistent grid size (0 when
+ * the kernel sizes its persistent grid at launch). */
 spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan);
 
 /* ------------------------------------------------------------------------ */

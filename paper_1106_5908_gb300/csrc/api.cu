@@ -267,6 +267,7 @@ struct spmv_matrix {
     int32_t *d_col = nullptr;
     void *d_val = nullptr;
     int32_t *d_err = nullptr;
+    uint64_t values_version = 0;  // incremented by spmv_set_values (batches copy values)
     std::vector<int32_t> h_rp;
     // plan
     double col_random = 0.0;  // column_randomness() of the pattern
@@ -331,6 +332,14 @@ struct spmv_batch {
     bool graph_valid = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // slot-major path: one copy of all matrices (chunks of matrix m start at
+    // slot_off[m]), the matrix of each chunk, and the member values versions the
+    // copy was laid out from
+    bool use_slots = false;
+    SlotTable slots;
+    int32_t *d_scmat = nullptr;
+    std::vector<int32_t> slot_off;
+    std::vector<uint64_t> vals_ver;
 };
 
 namespace {
@@ -867,6 +876,7 @@ spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *
     if (h->mirror32) CK(launch_convert(val, t, h->mirror32->d_val, kF32, h->nnz, s));
     h->valT_valid = false;
     h->valT_requested = false;
+    ++h->values_version;
     for (auto &kv : h->slots) kv.second.vals_valid = false;
     return SPMV_OK;
 }
@@ -1398,6 +1408,60 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
         rows += mats[m]->n_rows;
     }
     b->E = (rows && static_cast<double>(nnz) / rows < 20.0) ? 7 : 15;
+    SlotOps sops;
+    if (slot_ops_batched(vk, acc, 7, &sops)) {
+        // the slot-major chunk kernel over one concatenated copy of all matrices
+        b->E = 7;
+        b->use_slots = true;
+        b->slot_off.assign(static_cast<size_t>(count) + 1, 0);
+        b->vals_ver.assign(static_cast<size_t>(count), 0);
+        std::vector<ChunkDesc> d;
+        std::vector<uint32_t> lm;
+        std::vector<int32_t> cm;
+        for (int32_t m = 0; m < count; ++m) {
+            b->slot_off[m] = static_cast<int32_t>(d.size());
+            make_slot_chunks(mats[m]->h_rp.data(), mats[m]->n_rows, 7, d, lm, &b->slots.n_long, &b->slots.n_empty);
+            cm.resize(d.size(), m);
+        }
+        b->slot_off[count] = static_cast<int32_t>(d.size());
+        b->slots.n = static_cast<int32_t>(d.size());
+        const size_t nslots = d.size() * 32 * 7;
+        const size_t vb = (vk == kF64) ? 8 : 4;
+        bool ok = dmalloc(&b->slots.d, d.size()) == cudaSuccess && dmalloc(&b->slots.lmask, lm.size()) == cudaSuccess &&
+                  dmalloc(&b->d_scmat, cm.size()) == cudaSuccess &&
+                  cudaMalloc(&b->slots.vals, nslots * vb + 16) == cudaSuccess &&
+                  dmalloc(&b->slots.cols, nslots + 4) == cudaSuccess;
+        ok = ok && (d.empty() || cudaMemcpy(b->slots.d, d.data(), sizeof(ChunkDesc) * d.size(),
+                                            cudaMemcpyHostToDevice) == cudaSuccess);
+        ok = ok && (lm.empty() || cudaMemcpy(b->slots.lmask, lm.data(), 4 * lm.size(), cudaMemcpyHostToDevice) ==
+                                      cudaSuccess);
+        ok = ok && (cm.empty() || cudaMemcpy(b->d_scmat, cm.data(), 4 * cm.size(), cudaMemcpyHostToDevice) ==
+                                      cudaSuccess);
+        for (int32_t m = 0; ok && m < count; ++m) {
+            const int64_t off = b->slot_off[m], nch = b->slot_off[m + 1] - off;
+            ok = launch_slot_relayout(b->slots.d + off, 7, nch * 32 * 7, vk, mats[m]->d_val, mats[m]->d_col,
+                                      static_cast<char *>(b->slots.vals) + off * 32 * 7 * vb,
+                                      b->slots.cols + off * 32 * 7, nullptr) == cudaSuccess;
+            b->vals_ver[m] = mats[m]->values_version;
+        }
+        ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+        b->slots.vals_valid = true;
+        b->h_mats.resize(static_cast<size_t>(count));
+        for (int32_t m = 0; m < count; ++m)
+            b->h_mats[m] = MatRef{mats[m]->d_rp, mats[m]->d_col, mats[m]->d_val, nullptr, nullptr, nullptr, nullptr};
+        b->cur_x.assign(static_cast<size_t>(count), nullptr);
+        b->cur_y.assign(static_cast<size_t>(count), nullptr);
+        if (ok && (dmalloc(&b->d_mats, b->h_mats.size()) != cudaSuccess || dmalloc(&b->d_err, 1) != cudaSuccess))
+            ok = false;
+        if (ok && cudaMemset(b->d_err, 0, 4) != cudaSuccess) ok = false;
+        b->grid = 0;
+        if (!ok) {
+            spmv_batched_destroy(b);
+            return SPMV_ERR_ALLOC;
+        }
+        *out = b;
+        return SPMV_OK;
+    }
     if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) b->E = 15;
     if (!warp_ops(vk, vk, vk, acc, b->E, false, true, &ops)) {
         delete b;
@@ -1434,6 +1498,8 @@ void spmv_batched_destroy(spmv_batch_handle b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     free_chunks(b->chunks);
+    free_slots(b->slots);
+    cudaFree(b->d_scmat);
     cudaFree(b->d_mats);
     cudaFree(b->d_err);
     delete b;
@@ -1461,8 +1527,53 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
         CK(cudaMemcpyAsync(b->d_mats, b->h_mats.data(), sizeof(MatRef) * b->h_mats.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
     }
-    if (b->chunks.n == 0) return SPMV_OK;
     const int acc = (b->vk == kF32) ? kAccFF : kAccF64;
+    if (b->use_slots) {
+        if (b->slots.n == 0) return SPMV_OK;
+        // members given new values since the copy: lay their values out again
+        const size_t vb = (b->vk == kF64) ? 8 : 4;
+        for (int32_t m = 0; m < b->count; ++m)
+            if (b->mats[m]->values_version != b->vals_ver[m]) {
+                const int64_t off = b->slot_off[m], nch = b->slot_off[m + 1] - off;
+                CK(launch_slot_relayout(b->slots.d + off, 7, nch * 32 * 7, b->vk, b->mats[m]->d_val, nullptr,
+                                        static_cast<char *>(b->slots.vals) + off * 32 * 7 * vb, nullptr, s));
+                b->vals_ver[m] = b->mats[m]->values_version;
+            }
+        SlotOps sops;
+        if (!slot_ops_batched(b->vk, acc, 7, &sops)) return SPMV_ERR_UNSUPPORTED;
+        if (recapture) {
+            if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+            if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+            b->graph_valid = false;
+            SlotParams p{};
+            p.chunks = b->slots.d;
+            p.lmask = b->slots.lmask;
+            p.vals = b->slots.vals;
+            p.cols = b->slots.cols;
+            p.mats = b->d_mats;
+            p.cmat = b->d_scmat;
+            p.n_chunks = b->slots.n;
+            p.alpha = alpha;
+            p.beta = beta;
+            cudaStream_t cap;
+            CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t le = sops.launch(p, cap);
+                e = cudaStreamEndCapture(cap, &b->graph);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return SPMV_ERR_CUDA;
+            b->graph_valid = true;
+            b->cur_alpha = alpha;
+            b->cur_beta = beta;
+        }
+        CK(cudaGraphLaunch(b->exec, s));
+        return SPMV_OK;
+    }
+    if (b->chunks.n == 0) return SPMV_OK;
     WarpOps ops;
     if (!warp_ops(b->vk, b->vk, b->vk, acc, b->E, false, true, &ops)) return SPMV_ERR_UNSUPPORTED;
     if (recapture) {
@@ -1501,7 +1612,7 @@ spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan) {
     if (!b || !plan) return SPMV_ERR_INVALID_ARG;
     plan[0] = b->E;
     plan[1] = 256;
-    plan[2] = b->chunks.n;
+    plan[2] = b->use_slots ? b->slots.n : b->chunks.n;
     plan[3] = b->grid;
     return SPMV_OK;
 }

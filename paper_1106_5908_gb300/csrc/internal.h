@@ -92,6 +92,8 @@ struct SlotOps {
 // pre: the variant that loads each chunk's row map and old y before its chains
 // (row-mapped products).
 bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops);
+// The batched variant (vectors of the value type): FP64, FP32 float-float; E = 7.
+bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops);
 // Slot-major copies of the values (and, when cols_out is not null, the column
 // indices) of the regular chunks in `chunks` (ChunkDesc[n_slots / (32E)]).
 cudaError_t launch_slot_relayout(const void *chunks, int E, int64_t n_slots, int vk, const void *val,

@@ -5,6 +5,18 @@
 
 namespace spmv {
 
+bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops) {
+    if (vk == kF64 && acc == kAccF64 && E == 7) {
+        ops->launch = &SlotKernel<7, double, double, double, AccF64, false, true>::launch;
+        return true;
+    }
+    if (vk == kF32 && acc == kAccFF && E == 7) {
+        ops->launch = &SlotKernel<7, float, float, float, AccFF, false, true>::launch;
+        return true;
+    }
+    return false;
+}
+
 bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     if (pre) {
         // row-mapped products (the split's nonlocal part): FP64, E = 7

@@ -30,6 +30,8 @@ struct SlotParams {
     const void *vals;       // n_chunks * 32E values, slot-major (zero in padding)
     const int32_t *cols;    // n_chunks * 32E column indices, slot-major (zero in padding)
     MatRef m;               // the CRS itself (long and empty-row chunks), x, y, row map
+    const MatRef *mats;     // batched: the matrix table (index in cmat per chunk)
+    const int32_t *cmat;
     int32_t n_chunks;
     double alpha, beta;
 };
@@ -61,7 +63,9 @@ struct kSlotScan {
 
 // PRE: the row epilogue's operands (row map, old y) are loaded before the FMA
 // chains (row-mapped products: the nonlocal part of the split form).
-template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false>
+// BATCHED: chunks of many matrices in one launch; chunk c belongs to matrix
+// cmat[c] of the table mats (its own x, y and CRS arrays).
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false, bool BATCHED = false>
 __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
     constexpr int SL = 32 * E;
     static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
@@ -75,9 +79,11 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
     ACC *srow = s_rows[wib];
     const uint64_t pol = l2_evict_first_policy();
     const VT *__restrict__ vals = static_cast<const VT *>(p.vals);
-    const XT *__restrict__ x = static_cast<const XT *>(p.m.x);
-    YT *__restrict__ y = static_cast<YT *>(p.m.y);
     const double alpha = p.alpha, beta = p.beta;
+    auto mat_of = [&](int cc) -> MatRef {
+        if constexpr (BATCHED) return p.mats[p.cmat[cc]];
+        else return p.m;
+    };
     const bool plain = (alpha == 1.0 && beta == 0.0);
 
     auto regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
@@ -92,7 +98,11 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = ld_stream(b + e * 32, pol);
     };
-    auto gather = [&](const ChunkDesc &d, const int32_t (&cl)[E], XT (&xv)[E]) {
+    auto xptr_of = [&](int cc) -> const XT * {
+        if constexpr (BATCHED) return static_cast<const XT *>(p.mats[__ldg(p.cmat + cc)].x);
+        else return static_cast<const XT *>(p.m.x);
+    };
+    auto gather = [&](const XT *__restrict__ x, const ChunkDesc &d, const int32_t (&cl)[E], XT (&xv)[E]) {
         const int hi = regular(d) ? hi_of(d) : 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) xv[e] = (e < hi) ? __ldg(x + cl[e]) : XT(0);
@@ -111,15 +121,17 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
     {
         int32_t cl[E];
         load_cols(c, cl);
-        gather(dc, cl, xc);
+        gather(xptr_of(c), dc, cl, xc);
         load_vals(c, vc);
     }
     ChunkDesc dn{};
     uint32_t mn = 0;
+    const XT *xpn = nullptr;
     int32_t cn[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) cn[e] = 0;
     if (c + nwarps < n) {
+        xpn = xptr_of(c + nwarps);
         dn = load_desc(c + nwarps);
         mn = __ldg(p.lmask + static_cast<int64_t>(c + nwarps) * 32 + lane);
         load_cols(c + nwarps, cn);
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         XT xn[E];
         VT vn[E];
         if (c1 < n) {
-            gather(dn, cn, xn);
+            gather(xpn, dn, cn, xn);
             load_vals(c1, vn);
         } else {
 #pragma unroll
@@ -142,8 +154,10 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         }
         ChunkDesc d2{};
         uint32_t m2 = 0;
+        const XT *xp2 = nullptr;
         int32_t c2l[E];
         if (c2 < n) {
+            xp2 = xptr_of(c2);
             d2 = load_desc(c2);
             m2 = __ldg(p.lmask + static_cast<int64_t>(c2) * 32 + lane);
             load_cols(c2, c2l);
@@ -152,15 +166,18 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
             for (int e = 0; e < E; ++e) c2l[e] = 0;
         }
         // ---- chunk c ---------------------------------------------------------
+        const MatRef m = mat_of(c);
+        const XT *__restrict__ x = static_cast<const XT *>(m.x);
+        YT *__restrict__ y = static_cast<YT *>(m.y);
         const int r0 = dc.r0;
         const int r1 = dc.r1f & kChunkRowMask;
         if (dc.r1f & kChunkLong) {
-            long_row<VT, XT, YT, ACC, false>(p.m, dc, x, y, alpha, beta, plain, lane);
+            long_row<VT, XT, YT, ACC, false>(m, dc, x, y, alpha, beta, plain, lane);
         } else if (dc.r1f & kChunkEmpty) {
-            rows_per_lane<VT, XT, YT, ACC, false>(p.m, r0, r1, x, y, alpha, beta, plain, lane);
+            rows_per_lane<VT, XT, YT, ACC, false>(m, r0, r1, x, y, alpha, beta, plain, lane);
         } else {
             RowEpilogue<YT> epi;
-            if constexpr (PRE) epi.prefetch(y, p.m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
+            if constexpr (PRE) epi.prefetch(y, m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
             const int hi = hi_of(dc);
             const uint32_t mbits = mc & ((1u << E) - 1u);
             if constexpr (kSlotScan<E, VT, PRE>::value) {
@@ -177,7 +194,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
                 epi.store(y, srow, r1 - r0, alpha, beta, plain, lane);
             } else {
                 for (int q = lane; q < r1 - r0; q += 32)
-                    store_acc(y, r0 + q, srow[q], alpha, beta, plain, p.m.rmap);
+                    store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
             }
         }
         __syncwarp();  // the row buffer is free again
@@ -185,6 +202,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         mc = mn;
         dn = d2;
         mn = m2;
+        xpn = xp2;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             xc[e] = xn[e];
@@ -216,7 +234,7 @@ __global__ void __launch_bounds__(256) k_slot_relayout(const ChunkDesc *__restri
     }
 }
 
-template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false>
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false, bool BATCHED = false>
 struct SlotKernel {
     static int grid_limit() {
         static int cached = -1;
@@ -226,7 +244,7 @@ struct SlotKernel {
         if (cached >= 0 && cached_dev == dev) return cached;
         int per_sm = 0, sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot<E, VT, XT, YT, ACC, PRE>, 256, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot<E, VT, XT, YT, ACC, PRE, BATCHED>, 256, 0) !=
             cudaSuccess)
             return 0;
         cached = per_sm * sms;
@@ -238,7 +256,7 @@ struct SlotKernel {
         const int lim = grid_limit();
         if (lim <= 0) return cudaErrorInvalidConfiguration;
         const int want = (p.n_chunks + 7) / 8;
-        k_slot<E, VT, XT, YT, ACC, PRE><<<want < lim ? want : lim, 256, 0, s>>>(p);
+        k_slot<E, VT, XT, YT, ACC, PRE, BATCHED><<<want < lim ? want : lim, 256, 0, s>>>(p);
         return cudaGetLastError();
     }
 };

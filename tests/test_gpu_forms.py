@@ -263,6 +263,31 @@ def test_batched_256_full_size():
             assert_within(host(ys[m]), ref, bound, 1e-13, f"batch m={m} rep={rep}")
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_follows_member_values(dtype):
+    """New values set on one member handle after the batch was built reach the
+    next batched launch (the batch lays that member's values out again)."""
+    from paper_1106_5908_gb300 import Batch, Matrix
+    As = [W.batch_matrix(m, n, seed=9) for m, n in enumerate((3000, 5000, 800, 12000))]
+    npdt = np.float32 if dtype == "f32" else np.float64
+    mats = [Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(npdt), A.n_cols) for A in As]
+    B = Batch(mats)
+    xs = [W.uniform(A.n_cols, 60 + m).astype(npdt) for m, A in enumerate(As)]
+    xd = [dev(x) for x in xs]
+    ys = [torch.zeros(A.n_rows, dtype=xd[0].dtype, device="cuda") for A in As]
+    B.apply(xd, ys)
+    v2 = W.uniform(As[2].nnz, 61).astype(npdt)
+    mats[2].set_values(dev(v2))
+    B.apply(xd, ys)
+    torch.cuda.synchronize()
+    rel = 1e-6 if dtype == "f32" else 1e-13
+    for m, A in enumerate(As):
+        val = v2 if m == 2 else A.val.astype(npdt)
+        ref, bound = oracle.spmv(A.row_ptr, A.col_idx, val.astype(np.float64), xs[m].astype(np.float64),
+                                 with_bound=True)
+        assert_within(host(ys[m]), ref, bound, rel, f"member {m}")
+
+
 def test_batched_integer_bitexact():
     from paper_1106_5908_gb300 import Batch, Matrix
     As = [W.random_csr(n, n, seed=n, integer=True, max_len=20, long_rows=1, long_len=min(n, 4000))
