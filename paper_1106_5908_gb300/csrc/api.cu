@@ -649,11 +649,8 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
     if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
         int E = h->E;
         WarpOps ops;
-        // family 3 selects the three-stage kernel of the same chunking (with the
-        // row epilogue loaded ahead when rows are mapped)
-        const bool ok3 = h->family == 3 &&
-                         ((h->d_rmap && warp_ops(h->vk, xk, yk, acc, E + 200, false, false, &ops)) ||
-                          warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops));
+        // family 3 selects the three-stage kernel of the same chunking
+        const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
         if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) {
             E = 16;
             if (!warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) return SPMV_ERR_UNSUPPORTED;

@@ -28,8 +28,6 @@ bool tile_ops_f32(int xk, int yk, int acc, int R, int E, bool indirect, bool bat
     SPMV_F32_CASE(kF32, float, kAccF64, AccF64, 1, 15, false, false)
     SPMV_F32_CASE(kF64, double, kAccFF, AccFF, 1, 15, false, false)
     SPMV_F32_CASE(kF64, double, kAccF64, AccF64, 1, 15, false, false)
-    SPMV_F32_CASE(kF32, float, kAccFF, AccFF, 1, 15, true, false)
-    SPMV_F32_CASE(kF32, float, kAccFF, AccFF, 1, 15, false, true)
 #undef SPMV_F32_CASE
     return false;
 }

@@ -1,7 +1,6 @@
 // Compiled configurations of the tile kernel for FP64 values and vectors: the
-// plain product (group width 1), block vectors (group width 2..32), the
-// transposed apply of the reverse pass (values through a permutation) and the
-// batched persistent launch.
+// plain product (group width 1, plan family 2) and block vectors (group width
+// 2..32).
 #include "tile_kernel.cuh"
 
 namespace spmv {
@@ -28,8 +27,6 @@ bool tile_ops_f64(int R, int E, bool indirect, bool batched, TileOps *ops) {
     SPMV_F64_CASE(8, 15, false, false)
     SPMV_F64_CASE(16, 15, false, false)
     SPMV_F64_CASE(32, 15, false, false)
-    SPMV_F64_CASE(1, 15, true, false)
-    SPMV_F64_CASE(1, 15, false, true)
 #undef SPMV_F64_CASE
     return false;
 }

@@ -1,8 +1,7 @@
 // Compiled configurations of the warp-chunk kernels for FP64 values and
-// vectors: the pipelined kernels (odd E; E + 100 three-stage, E + 200 three-stage
-// for row-mapped products) and the unpipelined one (E = 8, 16), for the plain
-// product, the transposed apply of the reverse pass (values through a
-// permutation) and the batched launch.
+// vectors: the pipelined kernels (odd E; E + 100 three-stage) and the
+// unpipelined one (E = 8, 16), for the plain product, the transposed apply of the
+// reverse pass (values through a permutation) and the batched launch.
 #include "pipe_kernel.cuh"
 #include "warp_kernel.cuh"
 
@@ -23,11 +22,6 @@ bool warp_ops_f64(int E, bool indirect, bool batched, WarpOps *ops) {
     SPMV_P3(11, false)
     SPMV_P3(15, false)
 #undef SPMV_P3
-    // E + 200: three-stage kernel with the row epilogue loaded ahead (row-mapped)
-    if (E == 215 && !indirect && !batched) {
-        ops->launch = &Pipe3Kernel<15, double, double, double, AccF64, false, false, true>::launch;
-        return true;
-    }
 #define SPMV_W(E_, IND_, BAT_)                                                             \
     if (E == E_ && indirect == IND_ && batched == BAT_) {                                  \
         ops->launch = &WarpKernel<E_, double, double, double, AccF64, IND_, BAT_>::launch; \

@@ -227,12 +227,7 @@ struct Pipe3Layout {
 // the SM's 256 KB to L1, which holds the x lines near columns reuse)
 template <int E> struct Pipe3Warps { static constexpr int value = 8; };
 
-// PRE: load the row epilogue's operands (row map, old y) before the FMA chains;
-// used for row-mapped products (the nonlocal pass of the split form), where each
-// finished row costs two dependent loads.  Kept out of the other instances,
-// whose FMA chains run measurably slower with the extra live registers.
-template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED,
-          bool PRE = false>
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
 __global__ void __launch_bounds__(32 * Pipe3Warps<E>::value, Pipe3Layout<E, VT, Pipe3Warps<E>::value>::min_blocks)
 k_pipe3(const WarpParams p) {
     static_assert(E % 2 == 1, "odd E: conflict-free strided shared-memory reads");
@@ -367,8 +362,6 @@ k_pipe3(const WarpParams p) {
             const int w0 = off >> 5, sh = off & 31;
             const uint64_t win = (static_cast<uint64_t>(smk[w0 + 1]) << 32) | smk[w0];
             const uint32_t mbits = static_cast<uint32_t>(win >> sh) & ((1u << E) - 1u);
-            RowEpilogue<YT> epi;
-            if constexpr (PRE) epi.prefetch(y, m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
             VT vals[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) vals[e] = (e >= lo && e < hi) ? sv[off + e] : VT(0);
@@ -376,12 +369,7 @@ k_pipe3(const WarpParams p) {
             const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
             chunk_lane<E, VT, XT, ACC>(vals, xcur, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
-            if constexpr (PRE) {
-                epi.store(y, srow, r1 - r0, alpha, beta, plain, lane);
-            } else {
-                for (int q = lane; q < r1 - r0; q += 32)
-                    store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
-            }
+            for (int q = lane; q < r1 - r0; q += 32) store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
         }
         __syncwarp();  // stage s and the row buffer are free again
 #pragma unroll
@@ -390,12 +378,11 @@ k_pipe3(const WarpParams p) {
     }
 }
 
-template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED,
-          bool PRE = false>
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
 struct Pipe3Kernel {
     static constexpr int WPB = Pipe3Warps<E>::value;
     using L = Pipe3Layout<E, VT, WPB>;
-    static constexpr auto fn = k_pipe3<E, VT, XT, YT, ACC, INDIRECT, BATCHED, PRE>;
+    static constexpr auto fn = k_pipe3<E, VT, XT, YT, ACC, INDIRECT, BATCHED>;
     static int grid_limit() {
         static int cached = -1;
         static int cached_dev = -1;
