@@ -387,10 +387,11 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 // with E = 7 entries per lane for mean row lengths below 10 and E = 9 above
 // (measured against the staged chunk kernels: Hamiltonian-like 150.6 vs
 // 196.6 us, 7-point 71.9 vs 74.3 us, 27-point 139.6 vs 159.2 us; E = 11, 13, 15
-// lose to 9 on all three).  FP32 storage: the slot-major kernel with E = 15 for
-// scattered columns (140.2 vs 152.1 us on the Hamiltonian-like matrix), the
-// two-stage staged kernel with E = 15 on stencils (56.2 vs 57.0 us on the
-// 7-point, 103.3 vs 103.6 us on the 27-point matrix).  The row-vector kernel's
+// lose to 9 on all three).  FP32 storage: the slot-major kernel with E = 7 for
+// scattered columns (133 vs 138 us for E = 15 and 152 us for the staged kernel on
+// the Hamiltonian-like matrix), the two-stage staged kernel with E = 15 on
+// stencils (56.2 vs 57.0 us on the 7-point, 103.3 vs 103.6 us on the 27-point
+// matrix).  The row-vector kernel's
 // lanes per row T (family 1) is the power of two nearest half the mean row
 // length, used when chosen explicitly.
 void autotune(spmv_matrix *h) {
@@ -401,7 +402,7 @@ void autotune(spmv_matrix *h) {
     const bool scattered = h->col_random > 0.25;
     if (h->vk == kF32) {
         h->family = scattered ? 4 : 0;
-        h->E = 15;
+        h->E = scattered ? 7 : 15;
     } else {
         h->family = 4;
         h->E = (mean < 10.0) ? 7 : 9;

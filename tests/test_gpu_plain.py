@@ -199,7 +199,7 @@ def test_autotuner_choices():
     for A, want in ((H, (4, 9)), (L3, (4, 7)), (S27, (4, 9))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols).info()
         assert (info["family"], info["E"]) == want
-    for A, want in ((H, (4, 15)), (L3, (0, 15)), (S27, (0, 15))):
+    for A, want in ((H, (4, 7)), (L3, (0, 15)), (S27, (0, 15))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
         assert (info["family"], info["E"]) == want
 
