@@ -478,6 +478,7 @@ SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s, bool transposed = fa
                                         s) == cudaSuccess;
         if (!ok) {
             free_slots(t);
+            (void)cudaGetLastError();  // a failed allocation must not surface at a later launch check
             return nullptr;
         }
         t.vals_valid = true;
@@ -629,10 +630,11 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     SlotOps sops;
-    if (h->family == 4 && ((h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, true, &sops)) ||
-                           slot_ops(h->vk, xk, yk, acc, h->E, false, &sops))) {
-        SlotTable *t = get_slots(h, h->E, s);
-        if (!t) return SPMV_ERR_ALLOC;
+    SlotTable *t = nullptr;
+    if (h->family == 4 &&
+        ((h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, true, &sops)) ||
+         slot_ops(h->vk, xk, yk, acc, h->E, false, &sops)) &&
+        (t = get_slots(h, h->E, s)) != nullptr) {
         SlotParams sp{};
         sp.chunks = t->d;
         sp.lmask = t->lmask;
@@ -645,10 +647,12 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
         return sops.launch(sp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     }
     // the staged chunk kernels (also family 4 in the vector and accumulator
-    // combinations the slot-major kernel is not compiled for: FP32 storage with
-    // an FP64 result or FP64 accumulation)
+    // combinations the slot-major kernel is not compiled for, FP32 storage with
+    // an FP64 result or FP64 accumulation, and when its copy could not be
+    // allocated)
     if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
         int E = h->E;
+        if (h->family == 4 && E != 7 && E != 15) E = 15;
         WarpOps ops;
         // family 3 selects the three-stage kernel of the same chunking
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
@@ -779,12 +783,12 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     SlotOps sops;
-    if (h->family == 4 && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops)) {
-        if (!get_slots(h, h->E, nullptr)) return SPMV_ERR_ALLOC;
+    if (h->family == 4 && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops) &&
+        get_slots(h, h->E, nullptr))
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
-    }
     if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
         int E = h->E;
+        if (h->family == 4 && E != 7 && E != 15) E = 15;
         WarpOps ops;
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
         if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) E = 16;
