@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libspmv.so")
 
-SOURCES = ["k_warp_f64.cu", "k_warp_f32.cu", "k_tile_f64.cu", "k_tile_f32.cu", "k_slot.cu", "k_aux.cu", "cg.cu",
+SOURCES = ["k_warp_f64.cu", "k_warp_f32.cu", "k_tile_f64.cu", "k_tile_f32.cu", "k_slot.cu", "k_sell.cu", "k_aux.cu", "cg.cu",
            "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -17,6 +17,7 @@
 #include "cg.h"
 #include "warp_kernel.cuh"
 #include "slot_kernel.cuh"
+#include "sell_kernel.cuh"
 
 namespace spmv {
 int64_t transpose_work_len(int32_t n_cols);
@@ -99,6 +100,20 @@ struct SlotTable {
     int32_t *cols = nullptr;    // n * 32E column indices, slot-major
     int32_t n = 0;
     int32_t n_long = 0, n_empty = 0;
+    bool vals_valid = false;
+};
+
+// Sorted row-slice copy of a matrix for plan family 5 (per window sigma).
+struct SellTable {
+    int2 *d = nullptr;          // per slice: first slot row and width (width < 0: long row)
+    int32_t *srows = nullptr;   // kSellC rows per slice (-1: none)
+    int32_t *cstart = nullptr;  // n_ctas + 1: first slice of each CTA of a launch
+    int32_t n_ctas = 0;
+    void *vals = nullptr;       // slot_rows * 32 values
+    int32_t *cols = nullptr;    // slot_rows * 32 column indices
+    int32_t n = 0;
+    int32_t n_long = 0;
+    int64_t slot_rows = 0;
     bool vals_valid = false;
 };
 
@@ -218,6 +233,103 @@ void make_slot_chunks(const int32_t *rp, int32_t n_rows, int E, std::vector<Chun
     }
 }
 
+// Rows longer than this are summed by a whole warp from the CRS arrays instead
+// of by one lane of a slice.
+constexpr int32_t kSellLongRow = 128;
+
+// Slices of the sorted row-slice layout: in each window of sigma rows, the rows
+// of at most kSellLongRow entries ordered by length (longest first, ties in row
+// order) and cut into slices of kSellC; each longer row is a slice of its own
+// (width -1, x = the row).  Slot rows are numbered consecutively over the slices
+// after kSellU rows of padding (a short block loads the slot rows before it).
+// Returns false when the slot rows do not fit in int32.
+bool make_sell_slices(const int32_t *rp, int32_t n_rows, int32_t sigma, std::vector<int2> &out,
+                      std::vector<int32_t> &srows, int32_t *n_long, int64_t *slot_rows) {
+    int64_t off = kSellU;
+    std::vector<int32_t> idx;
+    for (int64_t w0 = 0; w0 < n_rows; w0 += sigma) {
+        const int32_t w1 = static_cast<int32_t>(std::min<int64_t>(n_rows, w0 + sigma));
+        idx.clear();
+        for (int32_t r = static_cast<int32_t>(w0); r < w1; ++r) {
+            if (rp[r + 1] - rp[r] > kSellLongRow) {
+                out.push_back(make_int2(r, -1));
+                srows.insert(srows.end(), kSellC, -1);
+                ++*n_long;
+            } else {
+                idx.push_back(r);
+            }
+        }
+        std::stable_sort(idx.begin(), idx.end(),
+                         [rp](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+        for (size_t i = 0; i < idx.size(); i += kSellC) {
+            const int32_t w = rp[idx[i] + 1] - rp[idx[i]];
+            if (off > INT32_MAX) return false;
+            out.push_back(make_int2(static_cast<int32_t>(off), w));
+            for (size_t l = 0; l < kSellC; ++l) srows.push_back(i + l < idx.size() ? idx[i + l] : -1);
+            off += w;
+        }
+    }
+    *slot_rows = off;
+    return off <= INT32_MAX;
+}
+
+// Padding of the sorted row-slice layout (stored slots / entries - 1) from the
+// row lengths alone: per window, a histogram of lengths gives every slice's width.
+double sell_padding(const int32_t *rp, int32_t n_rows, int32_t sigma) {
+    int64_t slots = 0, used = 0;
+    std::vector<int32_t> hist(kSellLongRow + 1);
+    for (int64_t w0 = 0; w0 < n_rows; w0 += sigma) {
+        const int32_t w1 = static_cast<int32_t>(std::min<int64_t>(n_rows, w0 + sigma));
+        std::fill(hist.begin(), hist.end(), 0);
+        for (int32_t r = static_cast<int32_t>(w0); r < w1; ++r) {
+            const int32_t len = rp[r + 1] - rp[r];
+            if (len > kSellLongRow) continue;
+            ++hist[len];
+            used += len;
+        }
+        // walk the lengths from the longest: every kSellC-th row opens a slice of its width
+        int64_t seen = 0;
+        for (int32_t len = kSellLongRow; len >= 0; --len) {
+            const int64_t c = hist[len];
+            if (c == 0) continue;
+            const int64_t opened = (seen + c + kSellC - 1) / kSellC - (seen + kSellC - 1) / kSellC;
+            slots += opened * kSellC * len;
+            seen += c;
+        }
+    }
+    return used ? static_cast<double>(slots) / used - 1.0 : 0.0;
+}
+
+// Contiguous slice ranges of equal work for G CTAs: ws[g] is the first slice
+// of CTA g.  A slice's work is its slots plus one slot row for its descriptor,
+// rows and stores; a long row's is its entries plus the same.
+void sell_ranges(const std::vector<int2> &d, const int32_t *rp, int G, std::vector<int32_t> &ws) {
+    std::vector<int64_t> pre(d.size() + 1, 0);
+    for (size_t i = 0; i < d.size(); ++i) {
+        const int64_t wk = d[i].y >= 0 ? (static_cast<int64_t>(d[i].y) + 1) * kSellC
+                                       : static_cast<int64_t>(rp[d[i].x + 1] - rp[d[i].x]) + kSellC;
+        pre[i + 1] = pre[i] + wk;
+    }
+    const int64_t total = pre.back();
+    ws.assign(static_cast<size_t>(G) + 1, 0);
+    size_t i = 0;
+    for (int g = 1; g < G; ++g) {
+        const int64_t target = total * g / G;
+        while (i < d.size() && pre[i] < target) ++i;
+        ws[g] = static_cast<int32_t>(i);
+    }
+    ws[G] = static_cast<int32_t>(d.size());
+}
+
+void free_sell(SellTable &t) {
+    cudaFree(t.d);
+    cudaFree(t.srows);
+    cudaFree(t.cstart);
+    cudaFree(t.vals);
+    cudaFree(t.cols);
+    t = SellTable();
+}
+
 void free_slots(SlotTable &t) {
     cudaFree(t.d);
     cudaFree(t.lmask);
@@ -280,6 +392,8 @@ struct spmv_matrix {
     std::map<int, ChunkTable> chunksT;                  // E -> warp chunks of A^T
     std::map<int, SlotTable> slots;                     // E -> slot-major copy (family 4)
     std::map<int, SlotTable> slotsT;                    // E -> slot-major copy of A^T (reverse pass)
+    std::map<int, SellTable> sells;                     // sigma -> sorted row-slice copy (family 5)
+    int32_t sigma = 4096;                               // family 5: rows per sorting window
     int32_t *d_rmap = nullptr;                          // output row of each stored row
     // transposed structure (built on first use)
     bool has_T = false;
@@ -383,23 +497,32 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 }
 
 // Autotuner: from the row-length histogram and the column scatter choose the
-// kernel and its work per lane.  FP64: the slot-major chunk kernel (family 4)
-// with E = 7 entries per lane for mean row lengths below 10 and E = 9 above
-// (measured against the staged chunk kernels: Hamiltonian-like 150.6 vs
-// 196.6 us, 7-point 71.9 vs 74.3 us, 27-point 139.6 vs 159.2 us; E = 11, 13, 15
-// lose to 9 on all three).  FP32 storage: the slot-major kernel with E = 7 for
-// scattered columns (133 vs 138 us for E = 15 and 152 us for the staged kernel on
-// the Hamiltonian-like matrix), the two-stage staged kernel with E = 15 on
-// stencils (56.2 vs 57.0 us on the 7-point, 103.3 vs 103.6 us on the 27-point
-// matrix).  The row-vector kernel's
-// lanes per row T (family 1) is the power of two nearest half the mean row
-// length, used when chosen explicitly.
+// kernel and its work per lane.
+//   Columns near the previous row's (stencils, banded matrices): the sorted
+//   row-slice kernel (family 5, windows of 4096 rows), when its padding is at
+//   most 10 %: 7-point 160^3 69.7 against 71.3 us (FP64) and 53.8 against
+//   55.8 us (FP32 storage), 27-point 128^3 113.0 against 139.1 us and 89.6
+//   against 102.9 us, against the best chunk kernels.
+//   Scattered columns: one row per lane gathers x from as many places as the
+//   slice has rows, so the slot-major chunk kernel (family 4) stays ahead
+//   (Hamiltonian-like 150.4 against 167.3 us): FP64 with E = 7 entries per lane
+//   for mean row lengths below 10 and E = 9 above (against the staged chunk
+//   kernels 150.6 vs 196.6 us; E = 11, 13, 15 lose to 9), FP32 storage with
+//   E = 7 (133 vs 138 us for E = 15, 152 us for the staged kernel).
+//   Otherwise: family 4 as above for FP64, the two-stage staged chunk kernel
+//   with E = 15 for FP32 storage.
+// The row-vector kernel's lanes per row T (family 1) is the power of two
+// nearest half the mean row length, used when chosen explicitly.
+constexpr int32_t kSellSigma = 4096;
+constexpr double kSellMaxPadding = 0.10;
+
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
     const bool scattered = h->col_random > 0.25;
+    h->sigma = kSellSigma;
     if (h->vk == kF32) {
         h->family = scattered ? 4 : 0;
         h->E = scattered ? 7 : 15;
@@ -407,6 +530,8 @@ void autotune(spmv_matrix *h) {
         h->family = 4;
         h->E = (mean < 10.0) ? 7 : 9;
     }
+    if (!scattered && h->n_rows > 0 && sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) <= kSellMaxPadding)
+        h->family = 5;
 }
 
 // Share of entries (sampled rows) whose column is more than 8 away from every
@@ -494,6 +619,54 @@ SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s, bool transposed = fa
     return &t;
 }
 
+// The sorted row-slice copy for window sigma (built on first use; its values are
+// laid out again on the stream after spmv_set_values).
+SellTable *get_sell(spmv_matrix *h, int32_t sigma, cudaStream_t s) {
+    auto it = h->sells.find(sigma);
+    if (it == h->sells.end()) {
+        std::vector<int2> d;
+        std::vector<int32_t> sr;
+        SellTable t;
+        if (!make_sell_slices(h->h_rp.data(), h->n_rows, sigma, d, sr, &t.n_long, &t.slot_rows)) return nullptr;
+        t.n = static_cast<int32_t>(d.size());
+        SellOps o;
+        const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
+        t.n_ctas = sell_ops(h->vk, h->vk, h->vk, acc, &o) ? o.ctas_for(t.n) : 0;
+        if (t.n_ctas <= 0) return nullptr;
+        std::vector<int32_t> ws;
+        sell_ranges(d, h->h_rp.data(), t.n_ctas, ws);
+        const size_t nslots = static_cast<size_t>(t.slot_rows) * kSellC;
+        const size_t vb = (h->vk == kF64) ? 8 : 4;
+        bool ok = dmalloc(&t.d, d.size()) == cudaSuccess && dmalloc(&t.srows, sr.size()) == cudaSuccess &&
+                  dmalloc(&t.cstart, ws.size()) == cudaSuccess &&
+                  cudaMalloc(&t.vals, nslots * vb + 16) == cudaSuccess && dmalloc(&t.cols, nslots + 4) == cudaSuccess;
+        ok = ok && cudaMemcpy(t.cstart, ws.data(), 4 * ws.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        // the leading padding rows: value 0, column -1
+        ok = ok && cudaMemsetAsync(t.vals, 0, static_cast<size_t>(kSellU) * kSellC * vb, s) == cudaSuccess &&
+             cudaMemsetAsync(t.cols, 0xff, static_cast<size_t>(kSellU) * kSellC * 4, s) == cudaSuccess;
+        ok = ok && (d.empty() || cudaMemcpy(t.d, d.data(), sizeof(int2) * d.size(), cudaMemcpyHostToDevice) ==
+                                     cudaSuccess);
+        ok = ok && (sr.empty() || cudaMemcpy(t.srows, sr.data(), 4 * sr.size(), cudaMemcpyHostToDevice) == cudaSuccess);
+        ok = ok && launch_sell_relayout(t.d, t.srows, t.n, h->d_rp, h->vk, h->d_val, h->d_col, t.vals, t.cols, s) ==
+                       cudaSuccess;
+        if (!ok) {
+            free_sell(t);
+            (void)cudaGetLastError();  // a failed allocation must not surface at a later launch check
+            return nullptr;
+        }
+        t.vals_valid = true;
+        it = h->sells.emplace(sigma, t).first;
+    }
+    SellTable &t = it->second;
+    if (!t.vals_valid) {
+        if (launch_sell_relayout(t.d, t.srows, t.n, h->d_rp, h->vk, h->d_val, nullptr, t.vals, nullptr, s) !=
+            cudaSuccess)
+            return nullptr;
+        t.vals_valid = true;
+    }
+    return &t;
+}
+
 void free_chunk_map(std::map<int, ChunkTable> &tabs) {
     for (auto &kv : tabs) free_chunks(kv.second);
     tabs.clear();
@@ -566,6 +739,7 @@ void destroy_matrix(spmv_matrix *h) {
     free_chunk_map(h->chunksT);
     for (auto &kv : h->slots) free_slots(kv.second);
     for (auto &kv : h->slotsT) free_slots(kv.second);
+    for (auto &kv : h->sells) free_sell(kv.second);
     cudaFree(h->d_rmap);
     destroy_cg(h->cg);
     if (h->mirror32) destroy_matrix(h->mirror32);
@@ -629,9 +803,27 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
                        int yk, cudaStream_t s) {
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    if (h->family == 5 && !h->d_rmap) {
+        SellOps lops;
+        SellTable *lt = nullptr;
+        if (sell_ops(h->vk, xk, yk, acc, &lops) && (lt = get_sell(h, h->sigma, s)) != nullptr) {
+            SellParams lp{};
+            lp.slices = lt->d;
+            lp.srows = lt->srows;
+            lp.cstart = lt->cstart;
+            lp.n_ctas = lt->n_ctas;
+            lp.vals = lt->vals;
+            lp.cols = lt->cols;
+            lp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
+            lp.n_slices = lt->n;
+            lp.alpha = alpha;
+            lp.beta = beta;
+            return lops.launch(lp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+        }
+    }
     SlotOps sops;
     SlotTable *t = nullptr;
-    if (h->family == 4 &&
+    if ((h->family == 4 || h->family == 5) &&
         ((h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, true, &sops)) ||
          slot_ops(h->vk, xk, yk, acc, h->E, false, &sops)) &&
         (t = get_slots(h, h->E, s)) != nullptr) {
@@ -646,13 +838,13 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
         sp.beta = beta;
         return sops.launch(sp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     }
-    // the staged chunk kernels (also family 4 in the vector and accumulator
-    // combinations the slot-major kernel is not compiled for, FP32 storage with
-    // an FP64 result or FP64 accumulation, and when its copy could not be
-    // allocated)
-    if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
+    // the staged chunk kernels (also families 4 and 5 in the vector and
+    // accumulator combinations their kernels are not compiled for, FP32 storage
+    // with an FP64 result or FP64 accumulation, and when their copies could not
+    // be allocated)
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->d_rmap) {
         int E = h->E;
-        if (h->family == 4 && E != 7 && E != 15) E = 15;
+        if ((h->family == 4 || h->family == 5) && E != 7 && E != 15) E = 15;
         WarpOps ops;
         // family 3 selects the three-stage kernel of the same chunking
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
@@ -782,13 +974,16 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 // allocation happens while a stream is being captured.
 static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    SellOps lops;
+    if (h->family == 5 && !h->d_rmap && sell_ops(h->vk, xk, yk, acc, &lops) && get_sell(h, h->sigma, nullptr))
+        return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     SlotOps sops;
-    if (h->family == 4 && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops) &&
+    if ((h->family == 4 || h->family == 5) && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops) &&
         get_slots(h, h->E, nullptr))
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
-    if (h->family == 0 || h->family == 3 || h->family == 4 || h->d_rmap) {
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->d_rmap) {
         int E = h->E;
-        if (h->family == 4 && E != 7 && E != 15) E = 15;
+        if ((h->family == 4 || h->family == 5) && E != 7 && E != 15) E = 15;
         WarpOps ops;
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
         if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) E = 16;
@@ -880,6 +1075,7 @@ spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *
     h->valT_requested = false;
     ++h->values_version;
     for (auto &kv : h->slots) kv.second.vals_valid = false;
+    for (auto &kv : h->sells) kv.second.vals_valid = false;
     return SPMV_OK;
 }
 
@@ -905,6 +1101,15 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
                 rowcap = c.rowcap;
                 threads = c.threads;
             }
+        } else if (h->family == 5) {
+            SellTable *t = get_sell(h, h->sigma, nullptr);
+            if (t) {
+                nunits = t->n;
+                nlong = t->n_long;
+            }
+            E = h->sigma;
+            rowcap = kSellC;
+            if (cudaDeviceSynchronize() != cudaSuccess) return SPMV_ERR_CUDA;
         } else if (h->family == 4) {
             SlotTable *t = get_slots(h, E, nullptr);
             if (t) {
@@ -947,7 +1152,13 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 }
 
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
-    if (!h || family < 0 || family > 4) return SPMV_ERR_INVALID_ARG;
+    if (!h || family < 0 || family > 5) return SPMV_ERR_INVALID_ARG;
+    if (family == 5) {
+        if (param != 0 && (param < 32 || param > (1 << 20) || (param & (param - 1)))) return SPMV_ERR_INVALID_ARG;
+        h->family = 5;
+        h->sigma = param ? param : 4096;
+        return SPMV_OK;
+    }
     if (family == 4) {
         if (param != 0 && param != 7 && param != 9 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
         if (h->vk == kF32 && (param == 9 || param == 11)) return SPMV_ERR_INVALID_ARG;

@@ -99,6 +99,21 @@ bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops);
 cudaError_t launch_slot_relayout(const void *chunks, int E, int64_t n_slots, int vk, const void *val,
                                  const int32_t *col, void *vals_out, int32_t *cols_out, cudaStream_t s);
 
+struct SellParams;
+// One compiled configuration of the sorted row-slice kernel (plan family 5):
+// (F64, F64, F64) with FP64 FMAs and (F32, F32, F32) with float-float sums.
+struct SellOps {
+    cudaError_t (*launch)(const SellParams &, cudaStream_t);
+    int (*ctas_for)(int32_t n_slices);  // CTAs a launch over n_slices uses
+};
+bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops);
+// Slot-major copies of the values (and, when cols_out is not null, the column
+// indices) of the regular slices in `slices` (int2[n_slices]; srows: 32 rows per
+// slice) from the CRS arrays rp, val, col.
+cudaError_t launch_sell_relayout(const void *slices, const int32_t *srows, int32_t n_slices, const int32_t *rp,
+                                 int vk, const void *val, const int32_t *col, void *vals_out, int32_t *cols_out,
+                                 cudaStream_t s);
+
 cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk, int yk, int acc,
                           int T, cudaStream_t s);
 

@@ -1,0 +1,41 @@
+// Compiled configurations of the sorted row-slice kernel (plan family 5) and its
+// relayout kernel: FP64 values and vectors, and FP32 storage with float-float
+// accumulation.
+#include "sell_kernel.cuh"
+
+namespace spmv {
+
+bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops) {
+    if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64) {
+        ops->launch = &SellKernel<double, double, double, AccF64>::launch;
+        ops->ctas_for = &SellKernel<double, double, double, AccF64>::ctas_for;
+        return true;
+    }
+    if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF) {
+        ops->launch = &SellKernel<float, float, float, AccFF>::launch;
+        ops->ctas_for = &SellKernel<float, float, float, AccFF>::ctas_for;
+        return true;
+    }
+    return false;
+}
+
+cudaError_t launch_sell_relayout(const void *slices, const int32_t *srows, int32_t n_slices, const int32_t *rp,
+                                 int vk, const void *val, const int32_t *col, void *vals_out, int32_t *cols_out,
+                                 cudaStream_t s) {
+    if (n_slices <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (static_cast<int64_t>(n_slices) * kSellC + 255) / 256;
+    const int grid = static_cast<int>(want < 16LL * sms ? want : 16LL * sms);
+    const int2 *d = static_cast<const int2 *>(slices);
+    if (vk == kF64)
+        k_sell_relayout<double><<<grid, 256, 0, s>>>(d, srows, n_slices, rp, static_cast<const double *>(val), col,
+                                                     static_cast<double *>(vals_out), cols_out);
+    else
+        k_sell_relayout<float><<<grid, 256, 0, s>>>(d, srows, n_slices, rp, static_cast<const float *>(val), col,
+                                                    static_cast<float *>(vals_out), cols_out);
+    return cudaGetLastError();
+}
+
+}  // namespace spmv

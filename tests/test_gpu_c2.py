@@ -47,8 +47,8 @@ def test_c2_plain_f64(c2, m2):
     assert_within(host(y), ref2, bound2, 1e-13, "C2 alpha/beta")
 
 
-@pytest.mark.parametrize("plan", [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (0, 16), (0, 8),
-                                  (2, 7), (2, 15), (2, 31), (1, 2)])
+@pytest.mark.parametrize("plan", [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 256),
+                                  (5, 4096), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 2)])
 def test_c2_plans(c2, m2, plan):
     A, x, ref, bound = c2
     m2.set_plan(*plan)

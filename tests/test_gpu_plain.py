@@ -12,8 +12,9 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (0, 16), (0, 8), (2, 7), (2, 15),
-         (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 32), (5, 256), (5, 4096), (0, 16),
+         (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+N_CHUNK_PLANS = 16  # plans before the row-vector kernel
 
 
 def make(A, dtype=None):
@@ -41,7 +42,7 @@ def test_random_plans(shape, plan):
         assert_within(host(y), ref, bound, 1e-13, f"plan {plan} a={alpha} b={beta}")
 
 
-@pytest.mark.parametrize("plan", PLANS[:13])
+@pytest.mark.parametrize("plan", PLANS[:N_CHUNK_PLANS])
 @pytest.mark.parametrize("long_len", [253, 257, 509, 513, 1791, 1793, 3841, 9000, 40000])
 def test_long_rows(plan, long_len):
     """Rows longer than a tile take the CTA-wide path; mixed with short ones."""
@@ -59,6 +60,9 @@ def test_long_rows(plan, long_len):
     elif plan[0] == 4:
         # slot-major chunks start at the row's first entry
         assert info["long_rows"] == int((np.diff(A.row_ptr) > 32 * plan[1]).sum())
+    elif plan[0] == 5:
+        # rows of more than 128 entries leave the sorted slices
+        assert info["long_rows"] == int((np.diff(A.row_ptr) > 128).sum())
     else:
         # a row is long when it does not fit 32*E slots from the aligned start
         slots = 32 * plan[1]
@@ -189,19 +193,31 @@ def test_laplace3d_160_fp32(c3):
 
 
 def test_autotuner_choices():
-    """The tuner picks the slot-major chunk kernel for FP64, with 7 entries per
-    lane for short rows and 9 otherwise; for FP32 storage the slot-major kernel
-    when the columns are scattered and the staged two-stage kernel on stencils."""
+    """The tuner picks the sorted row-slice kernel (windows of 4096 rows) for
+    matrices whose columns stay near the previous row's (stencils), and for
+    scattered columns the slot-major chunk kernel: FP64 with 7 entries per lane
+    for short rows and 9 otherwise, FP32 storage with 7.  A matrix whose sorted
+    slices would pad more than 10 % keeps the chunk kernels."""
     from paper_1106_5908_gb300 import Matrix
     H = W.hamiltonian_like(50000, seed=3)
     L3 = W.laplace3d(24)
     S27 = W.stencil27(20, seed=1)
-    for A, want in ((H, (4, 9)), (L3, (4, 7)), (S27, (4, 9))):
+    for A, want in ((H, (4, 9)), (L3, (5, 4096)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols).info()
         assert (info["family"], info["E"]) == want
-    for A, want in ((H, (4, 7)), (L3, (0, 15)), (S27, (0, 15))):
+    for A, want in ((H, (4, 7)), (L3, (5, 4096)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
         assert (info["family"], info["E"]) == want
+    # 100 rows of lengths 100, 99, ..., 1 with columns 0 .. len-1 (not scattered):
+    # one window, slices of widths 100 and 36 would store 8704 slots for 5050
+    # entries, so the tuner keeps the slot-major chunk kernel
+    n = 100
+    lens = np.arange(n, 0, -1, dtype=np.int64)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(lens)
+    col = np.concatenate([np.arange(l, dtype=np.int32) for l in lens])
+    info = Matrix.from_csr(rp, col, np.ones(rp[-1]), n).info()
+    assert info["family"] == 4
 
 
 @pytest.mark.parametrize("acc", ["ff", "f64"])
@@ -231,10 +247,10 @@ def test_fp32_widening_exact(acc, plan):
     assert np.array_equal(y[~nan], want[~nan]), np.flatnonzero(y[~nan] != want[~nan])[:8]
 
 
-@pytest.mark.parametrize("plan", [(4, 7), (4, 15)])
+@pytest.mark.parametrize("plan", [(4, 7), (4, 15), (5, 32), (5, 4096)])
 def test_slot_major_follows_new_values(plan):
-    """The slot-major copy (plan family 4) is laid out again after new values, in
-    FP64 and in FP32 storage."""
+    """The slot-major copies (plan families 4 and 5) are laid out again after new
+    values, in FP64 and in FP32 storage."""
     A = W.random_csr(5000, 4000, seed=41, max_len=40, long_rows=2, long_len=3000)
     x = W.uniform(A.n_cols, 1)
     for dt in (None, torch.float32):
