@@ -39,7 +39,7 @@ UNIT = "GB/s"
 # DRAM traffic of one launch of the plain FP64 chunk kernel on this workload, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_hash": "69645de6463d2734", "bytes_per_launch": 750995883,
+TRAFFIC = {"kernel_hash": "77daf72e1513b49f", "bytes_per_launch": 750929579,
            "source": "profiles/k_slot_f64_hamiltonian_c2.md (mean of 3 launches)"}
 
 
@@ -589,14 +589,23 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
 
 
 def run_only_plain(args, local_rank):
-    """Only the plain FP64 product on the Hamiltonian-like matrix, warm-up plus K
-    launches (the case a kernel profiler captures)."""
+    """Only the plain FP64 product, warm-up plus K launches (the case a kernel
+    profiler captures): on the Hamiltonian-like matrix (`--only plain`), the
+    160^3 7-point Poisson matrix (`--only poisson7`) or the 128^3 27-point
+    stencil (`--only stencil27`)."""
     import torch
     from paper_1106_5908_gb300 import Matrix
     from paper_1106_5908_gb300.build import build as build_lib
     torch.cuda.set_device(local_rank)
     build_lib()
-    A, x = c2_workload()
+    if args.only == "plain":
+        A, x = c2_workload()
+    elif args.only == "poisson7":
+        A = W.laplace3d(W.C3_GRID)
+        x = W.uniform(A.n_cols, W.SEED_C3_B)
+    else:
+        A = W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
+        x = W.uniform(A.n_cols, W.SEED_C5_X)
     M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
     xd = torch.as_tensor(x).cuda()
     y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
@@ -611,7 +620,7 @@ def run_only_plain(args, local_rank):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"only": "plain_f64", "ms_per_launch": ms, "plan": M.info(),
+    print(json.dumps({"only": f"{args.only}_f64", "n": A.n_rows, "nnz": A.nnz, "ms_per_launch": ms, "plan": M.info(),
                       "GBs": model.bytes_plain(A.n_rows, A.n_cols, A.nnz) / ms / 1e6}), flush=True)
 
 
@@ -676,8 +685,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=("plain",), default=None,
-                    help="run only the plain FP64 product (for kernel profiling)")
+    ap.add_argument("--only", choices=("plain", "poisson7", "stencil27"), default=None,
+                    help="run only the plain FP64 product on the Hamiltonian-like matrix, the 7-point "
+                         "or the 27-point matrix (for kernel profiling)")
     ap.add_argument("--study", choices=("ordering",), default=None,
                     help="natural / RCM / random ordering of the Hamiltonian-like matrix")
     ap.add_argument("--study-auto-only", action="store_true",
@@ -691,7 +701,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
-    if args.only == "plain":
+    if args.only is not None:
         run_only_plain(args, local_rank)
         return
     if args.study == "ordering":

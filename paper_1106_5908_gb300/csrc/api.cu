@@ -498,11 +498,15 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 
 // Autotuner: from the row-length histogram and the column scatter choose the
 // kernel and its work per lane.
-//   Columns near the previous row's (stencils, banded matrices): the sorted
-//   row-slice kernel (family 5, windows of 4096 rows), when its padding is at
-//   most 10 %: 7-point 160^3 69.7 against 71.3 us (FP64) and 53.8 against
-//   55.8 us (FP32 storage), 27-point 128^3 113.0 against 139.1 us and 89.6
-//   against 102.9 us, against the best chunk kernels.
+//   Columns near the previous row's (stencils, banded matrices) and at least
+//   12 entries per row: the sorted row-slice kernel (family 5, windows of 4096
+//   rows), when its padding is at most 10 % (27-point 128^3: 113.0 against
+//   139.1 us in FP64, 89.6 against 102.9 us with FP32 storage, against the best
+//   chunk kernels).  With short rows it gains little alone and loses next to
+//   other kernels: on the 7-point 160^3 matrix 69.3 against 71.5 us in a loop
+//   of products, but 74-80 against 70-74 us right after a kernel that wrote
+//   33 MB (the write-back of that kernel's dirty lines lands on a product
+//   already at 90 % of the copy bandwidth), and FP64 CG 109 against 105 ms.
 //   Scattered columns: one row per lane gathers x from as many places as the
 //   slice has rows, so the slot-major chunk kernel (family 4) stays ahead
 //   (Hamiltonian-like 150.4 against 167.3 us): FP64 with E = 7 entries per lane
@@ -515,6 +519,7 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 // nearest half the mean row length, used when chosen explicitly.
 constexpr int32_t kSellSigma = 4096;
 constexpr double kSellMaxPadding = 0.10;
+constexpr double kSellMinRowLength = 12.0;
 
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
@@ -530,7 +535,8 @@ void autotune(spmv_matrix *h) {
         h->family = 4;
         h->E = (mean < 10.0) ? 7 : 9;
     }
-    if (!scattered && h->n_rows > 0 && sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) <= kSellMaxPadding)
+    if (!scattered && mean >= kSellMinRowLength &&
+        sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) <= kSellMaxPadding)
         h->family = 5;
 }
 

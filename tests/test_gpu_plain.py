@@ -194,23 +194,24 @@ def test_laplace3d_160_fp32(c3):
 
 def test_autotuner_choices():
     """The tuner picks the sorted row-slice kernel (windows of 4096 rows) for
-    matrices whose columns stay near the previous row's (stencils), and for
-    scattered columns the slot-major chunk kernel: FP64 with 7 entries per lane
-    for short rows and 9 otherwise, FP32 storage with 7.  A matrix whose sorted
-    slices would pad more than 10 % keeps the chunk kernels."""
+    matrices whose columns stay near the previous row's (stencils) with at least
+    12 entries per row; otherwise the chunk kernels: FP64 the slot-major one with
+    7 entries per lane for short rows and 9 otherwise, FP32 storage the slot-major
+    one with 7 for scattered columns and the staged one with 15 on stencils.  A
+    matrix whose sorted slices would pad more than 10 % keeps the chunk kernels."""
     from paper_1106_5908_gb300 import Matrix
     H = W.hamiltonian_like(50000, seed=3)
     L3 = W.laplace3d(24)
     S27 = W.stencil27(20, seed=1)
-    for A, want in ((H, (4, 9)), (L3, (5, 4096)), (S27, (5, 4096))):
+    for A, want in ((H, (4, 9)), (L3, (4, 7)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols).info()
         assert (info["family"], info["E"]) == want
-    for A, want in ((H, (4, 7)), (L3, (5, 4096)), (S27, (5, 4096))):
+    for A, want in ((H, (4, 7)), (L3, (0, 15)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
         assert (info["family"], info["E"]) == want
-    # 100 rows of lengths 100, 99, ..., 1 with columns 0 .. len-1 (not scattered):
-    # one window, slices of widths 100 and 36 would store 8704 slots for 5050
-    # entries, so the tuner keeps the slot-major chunk kernel
+    # 100 rows of lengths 100, 99, ..., 1 with columns 0 .. len-1 (not scattered,
+    # 50.5 per row): one window, slices of widths 100 and 36 would store 8704
+    # slots for 5050 entries, so the tuner keeps the slot-major chunk kernel
     n = 100
     lens = np.arange(n, 0, -1, dtype=np.int64)
     rp = np.zeros(n + 1, np.int32)
