@@ -90,11 +90,12 @@ void spmv_destroy(spmv_handle h);
 spmv_status spmv_set_values(spmv_handle h, const void *val, spmv_dtype t, void *stream);
 
 /* Shape and plan of a handle.  plan[0..7] receives: kernel family (as for
- * spmv_set_plan), entries per lane or thread segment E, threads per CTA, number
- * of chunks or tiles, rows per chunk or tile cap, threads per row of the
- * row-vector kernel, number of rows longer than a chunk or tile, value dtype.
- * Any output may be NULL.  Builds the plan's chunk table if needed
- * (synchronises the device). */
+ * spmv_set_plan), entries per lane or thread segment E (family 5: the sorting
+ * window sigma), threads per CTA, number of chunks, tiles or slices, rows per
+ * chunk or tile cap (family 5: rows per slice), threads per row of the
+ * row-vector kernel, number of rows longer than a chunk or tile (family 5: rows
+ * of more than 128 entries), value dtype.  Any output may be NULL.  Builds the
+ * plan's chunk table if needed (synchronises the device). */
 spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64_t *nnz,
                           int32_t *plan);
 
@@ -112,7 +113,14 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  * family 4: slot-major warp-chunk kernel (values and column indices copied once
  *           into chunk-major, lane-interleaved order and loaded coalesced into
  *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 15);
- *           the copy is built on first use and its values follow spmv_set_values.
+ *           the copy is built on first use and its values follow spmv_set_values;
+ * family 5: sorted row-slice kernel (SELL-C-sigma with C = 64: in each window
+ *           of param rows, a power of two from 32 to 2^20, default 4096, the
+ *           rows ordered by length and stored 64 rows at a time, two rows per
+ *           lane; rows of more than 128 entries summed by a whole warp); FP64
+ *           and FP32 storage with float-float accumulation, other combinations
+ *           run the slot-major kernel; copy built on first use, values follow
+ *           spmv_set_values.
  * param 0 keeps a default.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
