@@ -198,7 +198,11 @@ spmv_status spmv_split_get_halo(spmv_split_handle hs, double *halo_out, void *st
 
 /* Y = alpha*A*X + beta*Y for nrhs right-hand sides stored interleaved:
  * X[j*nrhs + r], Y[i*nrhs + r] (row-major, leading dimension nrhs).
- * 1 <= nrhs <= 64.  vt: SPMV_F64 (X, Y FP64; FP64 values) only. */
+ * 1 <= nrhs <= 64.  vt: SPMV_F64 (X, Y FP64; FP64 values) only.  Groups of 4
+ * right-hand sides run on the sorted row slices of plan family 5 (built on first
+ * use, whatever the handle's plan) when they pad at most 10 % and, for scattered
+ * columns, X fits in L2; the rest on the tile kernel.  Results are unchanged up
+ * to summation order. */
 spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X, double beta,
                        void *Y, spmv_dtype vt, void *stream);
 

@@ -394,6 +394,7 @@ struct spmv_matrix {
     std::map<int, SlotTable> slotsT;                    // E -> slot-major copy of A^T (reverse pass)
     std::map<int, SellTable> sells;                     // sigma -> sorted row-slice copy (family 5)
     int32_t sigma = 4096;                               // family 5: rows per sorting window
+    double sell_pad = 1.0;                              // padding of sorted slices of 4096-row windows
     int32_t *d_rmap = nullptr;                          // output row of each stored row
     // transposed structure (built on first use)
     bool has_T = false;
@@ -528,6 +529,7 @@ void autotune(spmv_matrix *h) {
     h->T = T;
     const bool scattered = h->col_random > 0.25;
     h->sigma = kSellSigma;
+    h->sell_pad = h->n_rows > 0 ? sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) : 1.0;
     if (h->vk == kF32) {
         h->family = scattered ? 4 : 0;
         h->E = scattered ? 7 : 15;
@@ -535,9 +537,7 @@ void autotune(spmv_matrix *h) {
         h->family = 4;
         h->E = (mean < 10.0) ? 7 : 9;
     }
-    if (!scattered && mean >= kSellMinRowLength &&
-        sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) <= kSellMaxPadding)
-        h->family = 5;
+    if (!scattered && mean >= kSellMinRowLength && h->sell_pad <= kSellMaxPadding) h->family = 5;
 }
 
 // Share of entries (sampled rows) whose column is more than 8 away from every
@@ -1461,7 +1461,43 @@ spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (h->n_rows == 0) return SPMV_OK;
     if (nrhs == 1) return apply_impl(h, alpha, X, kF64, beta, Y, kF64, s);
-    for (int32_t c0 = 0; c0 < nrhs; c0 += 32) {
+    int32_t c0 = 0;
+    // Groups of 4 right-hand sides on the sorted row slices (one FMA chain per
+    // row and right-hand side, no carries), when the slices pad little and, for
+    // scattered columns, X fits in L2: each group gathers 32 bytes of a row of X
+    // per entry, which costs a DRAM burst apiece once X is out of L2, where the
+    // tile kernel reads whole rows of X once.  Measured (ms, slices against the
+    // tile kernel): 27-point 128^3 nrhs 4 / 8 / 16 / 32: 0.384 / 0.767 / 1.774 /
+    // 3.566 against 0.589 / 1.155 / 2.242 / 4.261; Hamiltonian-like (X of 134 MB
+    // per 4 right-hand sides) nrhs 4: 0.465 against 0.591, nrhs 8 / 16 / 32:
+    // 1.461 / 3.999 / 8.156 against 1.105 / 2.125 / 4.104.
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
+    const bool x_fits = static_cast<double>(h->n_cols) * nrhs * 8.0 <= 1.25 * l2;
+    SellTable *t = nullptr;
+    if (nrhs >= kSellR && h->sell_pad <= kSellMaxPadding && (h->col_random <= 0.25 || x_fits) &&
+        (t = get_sell(h, kSellSigma, s)) != nullptr) {
+        const bool vec = (nrhs % 2 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(Y) % 16 == 0);
+        SellParams b{};
+        b.slices = t->d;
+        b.srows = t->srows;
+        b.cstart = t->cstart;
+        b.vals = t->vals;
+        b.cols = t->cols;
+        b.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, nullptr, nullptr, nullptr};
+        b.n_slices = t->n;
+        b.n_ctas = t->n_ctas;
+        b.alpha = alpha;
+        b.beta = beta;
+        for (; c0 + kSellR <= nrhs; c0 += kSellR)
+            if (launch_sell_mr(b, static_cast<const double *>(X) + c0, static_cast<double *>(Y) + c0, nrhs, nrhs,
+                               vec, s) != cudaSuccess)
+                return SPMV_ERR_CUDA;
+    }
+    // the remaining right-hand sides (all of them without the slices): the tile
+    // kernel, up to 32 per launch
+    for (; c0 < nrhs; c0 += 32) {
         const int cnt = std::min(32, nrhs - c0);
         int R = 2;
         while (R < cnt) R <<= 1;

@@ -107,6 +107,12 @@ struct SellOps {
     int (*ctas_for)(int32_t n_slices);  // CTAs a launch over n_slices uses
 };
 bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops);
+// Block vectors on the sorted row slices, 4 right-hand sides:
+// Y[i*ldy + r] = alpha*sum_j a_ij X[j*ldx + r] + beta*Y[i*ldy + r], r = 0..3
+// (b carries the slices, alpha and beta; its x and y are not used).  vec: X, Y,
+// ldx and ldy allow 16-byte accesses.
+cudaError_t launch_sell_mr(const SellParams &b, const double *X, double *Y, int64_t ldx, int64_t ldy, bool vec,
+                           cudaStream_t s);
 // Slot-major copies of the values (and, when cols_out is not null, the column
 // indices) of the regular slices in `slices` (int2[n_slices]; srows: 32 rows per
 // slice) from the CRS arrays rp, val, col.

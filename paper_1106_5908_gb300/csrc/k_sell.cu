@@ -19,6 +19,15 @@ bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops) {
     return false;
 }
 
+cudaError_t launch_sell_mr(const SellParams &b, const double *X, double *Y, int64_t ldx, int64_t ldy, bool vec,
+                           cudaStream_t s) {
+    if (b.n_slices <= 0 || b.n_ctas <= 0) return cudaSuccess;
+    const SellMrParams q{b, X, Y, ldx, ldy};
+    if (vec) k_sell_mr<true><<<b.n_ctas, 256, 0, s>>>(q);
+    else k_sell_mr<false><<<b.n_ctas, 256, 0, s>>>(q);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sell_relayout(const void *slices, const int32_t *srows, int32_t n_slices, const int32_t *rp,
                                  int vk, const void *val, const int32_t *col, void *vals_out, int32_t *cols_out,
                                  cudaStream_t s) {

@@ -263,6 +263,216 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Block vectors on the same slices: Y[:, c0:c0+4] = alpha*A*X[:, c0:c0+4] +
+// beta*Y[:, c0:c0+4] for row-major X (leading dimension ldx) and Y (ldy).  Each
+// lane keeps 2 rows x 4 right-hand sides = 8 independent FMA chains and walks
+// its slices one slot row at a time; a slot's four x values are one 32-byte
+// sector (two 16-byte loads when VEC).  FP64 only.
+// ---------------------------------------------------------------------------
+constexpr int kSellR = 4;  // right-hand sides per pass
+
+struct SellMrParams {
+    SellParams b;   // slices, rows, copies, CRS (long rows), n_slices, cstart, alpha, beta
+    const double *X;
+    double *Y;
+    int64_t ldx, ldy;
+};
+
+__device__ __forceinline__ double2 ld_gather2(const double *p) {
+    double2 v;
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
+// A row too long for a slice, for 4 right-hand sides: lanes stride the row, then
+// a butterfly reduction of each sum.
+template <bool VEC>
+__device__ __forceinline__ void long_row_mr(const SellMrParams &q, int row, double alpha, double beta, bool plain,
+                                            int lane) {
+    const int32_t *__restrict__ col = q.b.m.col;
+    const double *__restrict__ val = static_cast<const double *>(q.b.m.vs);
+    const int k0 = __ldg(q.b.m.rp + row), k1 = __ldg(q.b.m.rp + row + 1);
+    double acc[kSellR];
+#pragma unroll
+    for (int r = 0; r < kSellR; ++r) acc[r] = 0.0;
+    for (int k = k0 + lane; k < k1; k += 32) {
+        const double v = __ldg(val + k);
+        const double *xp = q.X + static_cast<int64_t>(__ldg(col + k)) * q.ldx;
+#pragma unroll
+        for (int r = 0; r < kSellR; ++r) acc[r] = fma(v, __ldg(xp + r), acc[r]);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < kSellR; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0) {
+        double *yp = q.Y + static_cast<int64_t>(row) * q.ldy;
+#pragma unroll
+        for (int r = 0; r < kSellR; ++r)
+            yp[r] = plain ? acc[r] : (beta == 0.0 ? alpha * acc[r] : fma(alpha, acc[r], beta * yp[r]));
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) k_sell_mr(const SellMrParams q) {
+    constexpr int K = kSellK, C = kSellC, R = kSellR;
+    const SellParams &p = q.b;
+    const int lane = threadIdx.x & 31;
+    if (static_cast<int>(blockIdx.x) >= p.n_ctas) return;
+    const int s0 = __ldg(p.cstart + blockIdx.x) + (threadIdx.x >> 5);
+    const int n = __ldg(p.cstart + blockIdx.x + 1);
+    if (s0 >= n) return;
+    const uint64_t pol = l2_evict_first_policy();
+    const double *__restrict__ vals = static_cast<const double *>(p.vals);
+    const int32_t *__restrict__ cols = p.cols;
+    const double *__restrict__ X = q.X;
+    double *__restrict__ Y = q.Y;
+    const int64_t ldx = q.ldx, ldy = q.ldy;
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+
+    // cursor: slice s (descriptor off, w) and its slot row j (one per step)
+    struct Cur {
+        int s, off, w, j;
+    };
+    auto slice_of = [&](int s) { return s < n ? __ldg(p.slices + s) : make_int2(0, 0); };
+    auto has_slot = [&](const Cur &c) { return c.s < n && c.j < c.w; };
+    auto last_of = [](const Cur &c) { return c.j + 1 >= c.w; };
+    auto advance = [&](Cur &c, int2 &dnext) {
+        if (!last_of(c)) {
+            c.j += 1;
+            return;
+        }
+        c.s += 8;
+        c.off = dnext.x;
+        c.w = dnext.y;
+        c.j = 0;
+        dnext = slice_of(c.s + 8);
+    };
+    // steps without a slot (long rows, empty slices, past the end) read the
+    // leading padding row; nothing inspects the loaded columns before the gather
+    auto base_of = [&](const Cur &c) {
+        return has_slot(c) ? (static_cast<int64_t>(c.off) + c.j) * C + lane : static_cast<int64_t>(lane);
+    };
+    struct Set {
+        double v[K];
+        double x[K][R];
+        int32_t c[K];
+        int r[K];
+    };
+    auto load_cols = [&](const Cur &c, Set &S) {
+        const int32_t *b = cols + base_of(c);
+#pragma unroll
+        for (int h = 0; h < K; ++h) S.c[h] = ld_stream(b + h * 32, pol);
+    };
+    auto load_vals = [&](const Cur &c, Set &S) {
+        const double *b = vals + base_of(c);
+#pragma unroll
+        for (int h = 0; h < K; ++h) S.v[h] = ld_stream(b + h * 32, pol);
+    };
+    auto gather = [&](const Cur &c, Set &S) {
+        const bool ok = has_slot(c);
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+            if (ok && S.c[h] >= 0) {
+                const double *xp = X + static_cast<int64_t>(S.c[h]) * ldx;
+                if constexpr (VEC) {
+                    const double2 a = ld_gather2(xp), b2 = ld_gather2(xp + 2);
+                    S.x[h][0] = a.x;
+                    S.x[h][1] = a.y;
+                    S.x[h][2] = b2.x;
+                    S.x[h][3] = b2.y;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) S.x[h][r] = ld_gather(xp + r);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) S.x[h][r] = 0.0;
+            }
+        }
+    };
+    auto rows_of = [&](const Cur &c, Set &S) {
+        const bool ok = c.s < n && c.w >= 0 && last_of(c);
+#pragma unroll
+        for (int h = 0; h < K; ++h) S.r[h] = ok ? __ldg(p.srows + static_cast<int64_t>(c.s) * C + h * 32 + lane) : -1;
+    };
+
+    Cur ca{s0, 0, 0, 0};
+    {
+        const int2 d = slice_of(s0);
+        ca.off = d.x;
+        ca.w = d.y;
+    }
+    int2 dnext = slice_of(s0 + 8);
+    Cur cb = ca;
+    advance(cb, dnext);
+    Cur cc = cb;
+    advance(cc, dnext);
+
+    Set S0, S1;
+    rows_of(ca, S0);
+    load_cols(ca, S0);
+    gather(ca, S0);
+    load_vals(ca, S0);
+    load_cols(cb, S1);
+    rows_of(cb, S1);
+
+    double acc[K][R];
+#pragma unroll
+    for (int h = 0; h < K; ++h)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[h][r] = 0.0;
+    auto step = [&](Set &P, Set &Q) {
+        gather(cb, Q);
+        load_vals(cb, Q);
+        load_cols(cc, P);
+        if (ca.w < 0) {
+            long_row_mr<VEC>(q, ca.off, alpha, beta, plain, lane);
+        } else {
+            if (has_slot(ca)) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int h = 0; h < K; ++h) acc[h][r] = fma(P.v[h], P.x[h][r], acc[h][r]);
+            }
+            if (last_of(ca)) {
+#pragma unroll
+                for (int h = 0; h < K; ++h) {
+                    if (P.r[h] >= 0) {
+                        double *yp = Y + static_cast<int64_t>(P.r[h]) * ldy;
+                        double o[R];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const double a = acc[h][r];
+                            o[r] = plain ? a : (beta == 0.0 ? alpha * a : fma(alpha, a, beta * yp[r]));
+                        }
+                        if constexpr (VEC) {
+                            reinterpret_cast<double2 *>(yp)[0] = make_double2(o[0], o[1]);
+                            reinterpret_cast<double2 *>(yp)[1] = make_double2(o[2], o[3]);
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < R; ++r) yp[r] = o[r];
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[h][r] = 0.0;
+                }
+            }
+        }
+        rows_of(cc, P);
+        ca = cb;
+        cb = cc;
+        advance(cc, dnext);
+    };
+    while (ca.s < n) {
+        step(S0, S1);
+        if (ca.s >= n) break;
+        step(S1, S0);
+    }
+}
+
 // Slot-major copy of the regular slices: row h*32 + l of slice s, holding row
 // r, has entry rp[r] + j at slot (off + j)*64 + h*32 + l for j < len(r), value 0
 // and column -1 after it.  cols_out may be null (values only, after new values).

@@ -37,6 +37,31 @@ def test_spmm_small(nrhs):
         assert_within(host(Y).ravel(), ref.ravel(), bound.ravel(), 1e-13, f"nrhs={nrhs}")
 
 
+@pytest.mark.parametrize("nrhs", [4, 6, 7, 8])
+def test_spmm_stencil_and_padded(nrhs):
+    """Block vectors on the sorted row slices of a 27-point stencil (groups of 4
+    right-hand sides there, the rest on the tile kernel), and on a matrix whose
+    slices would pad too much (rows of lengths 200, 199, ..., 1 plus a long one:
+    the tile kernel alone)."""
+    S = W.stencil27(12, seed=nrhs)
+    n = 200
+    lens = np.arange(n, 0, -1, dtype=np.int64)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(lens)
+    rng = np.random.default_rng(nrhs)
+    col = np.concatenate([np.sort(rng.choice(300, int(l), replace=False)).astype(np.int32) for l in lens])
+    P = W.CRS(rp, col, rng.uniform(-1, 1, rp[-1]), 300)
+    for A in (S, P):
+        M = make(A)
+        X = W.uniform(0, 5, shape=(A.n_cols, nrhs))
+        Y0 = W.uniform(0, 6, shape=(A.n_rows, nrhs))
+        for alpha, beta in [(1.0, 0.0), (-2.0, 0.5)]:
+            ref, bound = oracle.spmm(*A.astuple(), X, alpha, beta, Y0, with_bound=True)
+            Y = dev(Y0)
+            M.spmm(dev(X), Y, alpha, beta)
+            assert_within(host(Y).ravel(), ref.ravel(), bound.ravel(), 1e-13, f"nrhs={nrhs} n={A.n_rows}")
+
+
 def test_spmm_integer_bitexact():
     A = W.random_csr(2000, 2000, seed=3, integer=True, max_len=30)
     M = make(A)
