@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "internal.h"
 #include "common.cuh"
 #include "cg.h"
 

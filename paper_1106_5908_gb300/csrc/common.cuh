@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "internal.h"
+#include "types.h"
 
 namespace spmv {
 

@@ -3,6 +3,7 @@
 // reverse pass, the on-device transposed-CRS build and value conversions.
 #include <algorithm>
 
+#include "internal.h"
 #include "common.cuh"
 #include "warp_kernel.cuh"
 

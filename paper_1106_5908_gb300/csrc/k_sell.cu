@@ -1,6 +1,7 @@
 // Compiled configurations of the sorted row-slice kernel (plan family 5) and its
 // relayout kernel: FP64 values and vectors, and FP32 storage with float-float
 // accumulation.
+#include "internal.h"
 #include "sell_kernel.cuh"
 
 namespace spmv {

@@ -1,6 +1,7 @@
 // Compiled configurations of the slot-major chunk kernel (plan family 4) and its
 // relayout kernel: FP64 values and vectors, and FP32 storage with float-float
 // accumulation.
+#include "internal.h"
 #include "slot_kernel.cuh"
 
 namespace spmv {

@@ -2,6 +2,7 @@
 // Products and row sums are carried in at least FP64-class precision, either by
 // one FP64 FMA per entry (operands widened on the integer pipe) or by the exact
 // float-float accumulator on the FP32 pipe.
+#include "internal.h"
 #include "tile_kernel.cuh"
 
 namespace spmv {

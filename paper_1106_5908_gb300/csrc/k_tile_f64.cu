@@ -1,6 +1,7 @@
 // Compiled configurations of the tile kernel for FP64 values and vectors: the
 // plain product (group width 1, plan family 2) and block vectors (group width
 // 2..32).
+#include "internal.h"
 #include "tile_kernel.cuh"
 
 namespace spmv {

@@ -1,5 +1,6 @@
 // Compiled configurations of the warp-chunk kernels for FP32-stored values and
 // vectors, with float-float (FP32 pipe) or FP64-FMA accumulation.
+#include "internal.h"
 #include "pipe_kernel.cuh"
 #include "warp_kernel.cuh"
 

@@ -2,6 +2,7 @@
 // vectors: the pipelined kernels (odd E; E + 100 three-stage) and the
 // unpipelined one (E = 8, 16), for the plain product, the transposed apply of the
 // reverse pass (values through a permutation) and the batched launch.
+#include "internal.h"
 #include "pipe_kernel.cuh"
 #include "warp_kernel.cuh"
 

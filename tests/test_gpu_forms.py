@@ -193,13 +193,14 @@ def test_autograd_fd_16cubed():
 # ---------------------------------------------------------------- solvers
 
 @pytest.mark.parametrize("grid", [24, W.C3_GRID])
-def test_ir_cg_and_cg(grid):
+@pytest.mark.parametrize("inner", [(1e-3, 500), (1e-4, 200)])
+def test_ir_cg_and_cg(grid, inner):
     from paper_1106_5908_gb300 import cg, ir_cg
     A = W.laplace3d(grid)
     M = make(A)
     b = W.uniform(A.n_rows, W.SEED_C3_B)
     bd = dev(b)
-    x, st = ir_cg(M, bd, outer_tol=1e-12, max_outer=50, inner_tol=1e-4, max_inner=200)
+    x, st = ir_cg(M, bd, outer_tol=1e-12, max_outer=50, inner_tol=inner[0], max_inner=inner[1])
     assert st["converged"], st
     xh = host(x)
     r = oracle.residual(*A.astuple(), b, xh)
