@@ -393,6 +393,8 @@ struct spmv_matrix {
     std::map<int, SlotTable> slots;                     // E -> slot-major copy (family 4)
     std::map<int, SlotTable> slotsT;                    // E -> slot-major copy of A^T (reverse pass)
     std::map<int, SellTable> sells;                     // sigma -> sorted row-slice copy (family 5)
+    std::map<int, SellTable> sellsT;                    // sigma -> sorted row-slice copy of A^T (reverse pass)
+    double sell_padT = -1.0;                            // padding of A^T's slices (computed on first use)
     int32_t sigma = 4096;                               // family 5: rows per sorting window
     double sell_pad = 1.0;                              // padding of sorted slices of 4096-row windows
     int32_t *d_rmap = nullptr;                          // output row of each stored row
@@ -626,21 +628,28 @@ SlotTable *get_slots(spmv_matrix *h, int E, cudaStream_t s, bool transposed = fa
 }
 
 // The sorted row-slice copy for window sigma (built on first use; its values are
-// laid out again on the stream after spmv_set_values).
-SellTable *get_sell(spmv_matrix *h, int32_t sigma, cudaStream_t s) {
-    auto it = h->sells.find(sigma);
-    if (it == h->sells.end()) {
+// laid out again on the stream after spmv_set_values).  transposed: the copy of
+// A^T, from the transposed structure and the values laid out in A^T order.
+SellTable *get_sell(spmv_matrix *h, int32_t sigma, cudaStream_t s, bool transposed = false) {
+    auto &tabs = transposed ? h->sellsT : h->sells;
+    const int32_t *h_rp = transposed ? h->h_rowT.data() : h->h_rp.data();
+    const int32_t nr = transposed ? h->n_cols : h->n_rows;
+    const int32_t *d_rp = transposed ? h->d_rowT : h->d_rp;
+    const int32_t *d_col = transposed ? h->d_colT : h->d_col;
+    const void *d_val = transposed ? h->d_valT : h->d_val;
+    auto it = tabs.find(sigma);
+    if (it == tabs.end()) {
         std::vector<int2> d;
         std::vector<int32_t> sr;
         SellTable t;
-        if (!make_sell_slices(h->h_rp.data(), h->n_rows, sigma, d, sr, &t.n_long, &t.slot_rows)) return nullptr;
+        if (!make_sell_slices(h_rp, nr, sigma, d, sr, &t.n_long, &t.slot_rows)) return nullptr;
         t.n = static_cast<int32_t>(d.size());
         SellOps o;
         const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
         t.n_ctas = sell_ops(h->vk, h->vk, h->vk, acc, &o) ? o.ctas_for(t.n) : 0;
         if (t.n_ctas <= 0) return nullptr;
         std::vector<int32_t> ws;
-        sell_ranges(d, h->h_rp.data(), t.n_ctas, ws);
+        sell_ranges(d, h_rp, t.n_ctas, ws);
         const size_t nslots = static_cast<size_t>(t.slot_rows) * kSellC;
         const size_t vb = (h->vk == kF64) ? 8 : 4;
         bool ok = dmalloc(&t.d, d.size()) == cudaSuccess && dmalloc(&t.srows, sr.size()) == cudaSuccess &&
@@ -653,20 +662,18 @@ SellTable *get_sell(spmv_matrix *h, int32_t sigma, cudaStream_t s) {
         ok = ok && (d.empty() || cudaMemcpy(t.d, d.data(), sizeof(int2) * d.size(), cudaMemcpyHostToDevice) ==
                                      cudaSuccess);
         ok = ok && (sr.empty() || cudaMemcpy(t.srows, sr.data(), 4 * sr.size(), cudaMemcpyHostToDevice) == cudaSuccess);
-        ok = ok && launch_sell_relayout(t.d, t.srows, t.n, h->d_rp, h->vk, h->d_val, h->d_col, t.vals, t.cols, s) ==
-                       cudaSuccess;
+        ok = ok && launch_sell_relayout(t.d, t.srows, t.n, d_rp, h->vk, d_val, d_col, t.vals, t.cols, s) == cudaSuccess;
         if (!ok) {
             free_sell(t);
             (void)cudaGetLastError();  // a failed allocation must not surface at a later launch check
             return nullptr;
         }
         t.vals_valid = true;
-        it = h->sells.emplace(sigma, t).first;
+        it = tabs.emplace(sigma, t).first;
     }
     SellTable &t = it->second;
     if (!t.vals_valid) {
-        if (launch_sell_relayout(t.d, t.srows, t.n, h->d_rp, h->vk, h->d_val, nullptr, t.vals, nullptr, s) !=
-            cudaSuccess)
+        if (launch_sell_relayout(t.d, t.srows, t.n, d_rp, h->vk, d_val, nullptr, t.vals, nullptr, s) != cudaSuccess)
             return nullptr;
         t.vals_valid = true;
     }
@@ -746,6 +753,7 @@ void destroy_matrix(spmv_matrix *h) {
     for (auto &kv : h->slots) free_slots(kv.second);
     for (auto &kv : h->slotsT) free_slots(kv.second);
     for (auto &kv : h->sells) free_sell(kv.second);
+    for (auto &kv : h->sellsT) free_sell(kv.second);
     cudaFree(h->d_rmap);
     destroy_cg(h->cg);
     if (h->mirror32) destroy_matrix(h->mirror32);
@@ -1549,14 +1557,40 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
             CK(launch_permute(h->d_val, h->d_perm, h->d_valT, h->nnz, h->vk, s));
             h->valT_valid = true;
             for (auto &kv : h->slotsT) kv.second.vals_valid = false;
+            for (auto &kv : h->sellsT) kv.second.vals_valid = false;
         }
         const bool ind = !h->valT_valid;
         h->valT_requested = true;
         bool done = false;
-        if (!ind) {
+        const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
+        if (!ind && h->col_random <= 0.25 && meanT >= kSellMinRowLength) {
+            // A^T of a stencil-like matrix with long rows: the sorted row-slice
+            // kernel on a row-slice copy of A^T (as the tuner picks for a forward
+            // product of such a matrix)
+            if (h->sell_padT < 0.0) h->sell_padT = sell_padding(h->h_rowT.data(), h->n_cols, kSellSigma);
+            SellOps lops;
+            const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
+            if (h->sell_padT <= kSellMaxPadding && sell_ops(h->vk, h->vk, h->vk, acc, &lops)) {
+                SellTable *t = get_sell(h, kSellSigma, s, true);
+                if (!t) return SPMV_ERR_ALLOC;
+                SellParams lp{};
+                lp.slices = t->d;
+                lp.srows = t->srows;
+                lp.cstart = t->cstart;
+                lp.vals = t->vals;
+                lp.cols = t->cols;
+                lp.m = MatRef{h->d_rowT, h->d_colT, h->d_valT, nullptr, g, grad_x, nullptr};
+                lp.n_slices = t->n;
+                lp.n_ctas = t->n_ctas;
+                lp.alpha = alpha;
+                lp.beta = 0.0;
+                if (lops.launch(lp, s) != cudaSuccess) return SPMV_ERR_CUDA;
+                done = true;
+            }
+        }
+        if (!ind && !done) {
             // A^T's values in its own order: the slot-major kernel on a slot-major
             // copy of A^T (E by A^T's mean row length, as for a forward product)
-            const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
             const int ES = (h->vk == kF32) ? 15 : ((meanT < 10.0) ? 7 : 9);
             SlotOps sops;
             const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
@@ -1579,7 +1613,6 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         if (!done) {
             WarpOps ops;
             const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
-            const double meanT = h->n_cols ? static_cast<double>(h->nnz) / h->n_cols : 0.0;
             int ET = (meanT < 20.0) ? 7 : 15;
             if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) ET = 15;
             if (!warp_ops(h->vk, h->vk, h->vk, acc, ET, ind, false, &ops)) return SPMV_ERR_UNSUPPORTED;
