@@ -1631,11 +1631,10 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         }
     }
     if (grad_val && h->nnz > 0) {
-        // the forward plan's chunks (any E): rows from the row-start bitmasks
-        const int E = (h->E == 7 || h->E == 8 || h->E == 11 || h->E == 15 || h->E == 16) ? h->E : 15;
-        ChunkTable *ct = get_chunks(h, E, false);
+        // warp chunks of kGradValE entries per lane: rows from the row-start bitmasks
+        ChunkTable *ct = get_chunks(h, kGradValE, false);
         if (!ct) return SPMV_ERR_ALLOC;
-        const int mwp = ((E + 3) / 4) * 4;
+        const int mwp = ((kGradValE + 3) / 4) * 4;
         if (launch_grad_val_chunks(h->d_rp, h->d_col, ct->d, ct->masks, mwp, ct->n, h->vk, g, x, alpha,
                                    grad_val, s) != cudaSuccess)
             return SPMV_ERR_CUDA;

@@ -87,7 +87,10 @@ cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int
                           cudaStream_t s);
 
 // grad_val over the warp chunks of A (ChunkDesc table + row-start bitmasks with
-// mwp words per chunk).
+// mwp words per chunk): chunks of kGradValE entries per lane, mwp = kGradValWords
+// (other tables are rejected with cudaErrorInvalidValue).
+constexpr int kGradValE = 7;
+constexpr int kGradValWords = 8;
 cudaError_t launch_grad_val_chunks(const int32_t *rp, const int32_t *col, const void *chunks,
                                    const uint32_t *masks, int mwp, int32_t n_chunks, int vk,
                                    const void *g, const void *x, double alpha, void *grad_val,

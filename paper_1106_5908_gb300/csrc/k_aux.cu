@@ -5,7 +5,7 @@
 
 #include "internal.h"
 #include "common.cuh"
-#include "warp_kernel.cuh"
+#include "slot_kernel.cuh"
 
 namespace spmv {
 
@@ -172,69 +172,126 @@ cudaError_t launch_gather(const double *x, const int32_t *map, double *halo, int
 // grad_val over the warp chunks of A: lanes take 32 consecutive entries at a
 // time (coalesced column loads and gradient stores); the row of each entry is the
 // chunk's first row plus the row starts (bits of the chunk's bitmask) up to it.
-// The kernel waits on its gathers, so it is held to three blocks (24 warps) per
-// SM (223 -> 181 us on the 27-point 128^3 pattern against two blocks).
-template <typename VT>
-__global__ void __launch_bounds__(256, 3) k_grad_val_chunks(const int32_t *__restrict__ rp,
-                                                         const int32_t *__restrict__ col,
-                                                         const ChunkDesc *__restrict__ chunks,
-                                                         const uint32_t *__restrict__ masks, int mwp,
-                                                         int32_t n_chunks, const VT *__restrict__ g,
-                                                         const VT *__restrict__ x, double alpha,
-                                                         VT *__restrict__ gv) {
+// Persistent warps walk the chunks c, c + nw, ...: the row-start words and
+// column indices of the next chunk (and the descriptors of the two after it) are
+// in flight while the current chunk's gathers and stores run, so a warp does not
+// wait on one whole load chain per chunk (27-point 128^3 pattern: 163 us; one
+// chunk per warp 176-181 us with DRAM 47 % busy; two chunks ahead, at 104
+// registers, 366 us; register copies between iterations instead of two sets
+// used in turn, 406 us).  MW: mask words per chunk (chunks of at most 32*MW slots).
+template <typename VT, int MW>
+__global__ void __launch_bounds__(256) k_grad_val_pipe(const int32_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ col,
+                                                       const ChunkDesc *__restrict__ chunks,
+                                                       const uint32_t *__restrict__ masks, int32_t n_chunks,
+                                                       const VT *__restrict__ g, const VT *__restrict__ x,
+                                                       double alpha, VT *__restrict__ gv) {
     const int lane = threadIdx.x & 31;
-    const int64_t w = static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5);
-    if (w >= n_chunks) return;
-    const ChunkDesc d = chunks[w];
-    const int r0 = d.r0;
-    const int r1 = d.r1f & kChunkRowMask;
+    const int nw = gridDim.x * 8;
+    int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= n_chunks) return;
+    const uint64_t pol = l2_evict_first_policy();
     const bool scaled = (alpha != 1.0);
     const VT a = static_cast<VT>(alpha);
-    if (d.r1f & kChunkLong) {
-        const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r0)) : __ldg(g + r0);
-        for (int k = d.k0 + lane; k < d.k1; k += 32) gv[k] = gr * __ldg(x + __ldg(col + k));
-        return;
-    }
-    if (d.r1f & kChunkEmpty) {
-        for (int r = r0 + lane; r < r1; r += 32) {
-            const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r)) : __ldg(g + r);
-            const int kb = __ldg(rp + r), ke = __ldg(rp + r + 1);
-            for (int k = kb; k < ke; ++k) gv[k] = gr * __ldg(x + __ldg(col + k));
-        }
-        return;
-    }
-    // all loads of the chunk are issued before any use (up to 16 words of 32)
-    constexpr int MAXW = 16;
-    const int base = d.k0 & ~3;
     const uint32_t below = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
-    uint32_t words[MAXW];
-    int32_t cc[MAXW];
+    auto regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
+    auto load_desc = [&](int cc) {
+        if (cc >= n_chunks) return ChunkDesc{0, 0, 0, kChunkEmpty};
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(chunks) + cc);
+        return ChunkDesc{q.x, q.y, q.z, q.w};
+    };
+    // row-start words and column indices of a regular chunk (-1: no entry)
+    auto load_body = [&](int cc, const ChunkDesc &d, uint32_t (&wds)[MW], int32_t (&cl)[MW]) {
+        const bool ok = cc < n_chunks && regular(d);
+        const int base = d.k0 & ~3;
 #pragma unroll
-    for (int wd = 0; wd < MAXW; ++wd) {
-        const int k = base + 32 * wd + lane;
-        words[wd] = (wd < mwp) ? __ldg(masks + w * mwp + wd) : 0u;
-        cc[wd] = (k >= d.k0 && k < d.k1) ? __ldg(col + k) : -1;
-    }
-    VT xv[MAXW], gr[MAXW];
-    int rows_before = 0;  // row starts in the chunk's earlier words
-#pragma unroll
-    for (int wd = 0; wd < MAXW; ++wd) {
-        const int row = r0 + rows_before + __popc(words[wd] & below) - 1;
-        xv[wd] = VT(0);
-        gr[wd] = VT(0);
-        if (cc[wd] >= 0) {
-            xv[wd] = __ldg(x + cc[wd]);
-            gr[wd] = __ldg(g + row);
+        for (int wd = 0; wd < MW; ++wd) {
+            const int k = base + 32 * wd + lane;
+            wds[wd] = ok ? __ldg(masks + static_cast<int64_t>(cc) * MW + wd) : 0u;
+            cl[wd] = (ok && k >= d.k0 && k < d.k1) ? ld_stream(col + k, pol) : -1;
         }
-        rows_before += __popc(words[wd]);
-    }
+    };
+
+    // chunk c's gathers, products and stores (its words and columns loaded one
+    // chunk earlier)
+    auto process = [&](const ChunkDesc &d, const uint32_t (&wds)[MW], const int32_t (&cl)[MW]) {
+        const int r0 = d.r0;
+        const int r1 = d.r1f & kChunkRowMask;
+        if (d.r1f & kChunkLong) {
+            const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r0)) : __ldg(g + r0);
+            for (int k = d.k0 + lane; k < d.k1; k += 32) gv[k] = gr * __ldg(x + __ldg(col + k));
+        } else if (d.r1f & kChunkEmpty) {
+            for (int r = r0 + lane; r < r1; r += 32) {
+                const VT gr = scaled ? static_cast<VT>(a * __ldg(g + r)) : __ldg(g + r);
+                const int kb = __ldg(rp + r), ke = __ldg(rp + r + 1);
+                for (int k = kb; k < ke; ++k) gv[k] = gr * __ldg(x + __ldg(col + k));
+            }
+        } else {
+            const int base = d.k0 & ~3;
+            VT xv[MW], gr[MW];
+            int rows_before = 0;  // row starts in the chunk's earlier words
 #pragma unroll
-    for (int wd = 0; wd < MAXW; ++wd) {
-        if (cc[wd] >= 0) {
-            const VT gg = scaled ? static_cast<VT>(a * gr[wd]) : gr[wd];
-            gv[base + 32 * wd + lane] = gg * xv[wd];
+            for (int wd = 0; wd < MW; ++wd) {
+                const int row = r0 + rows_before + __popc(wds[wd] & below) - 1;
+                xv[wd] = VT(0);
+                gr[wd] = VT(0);
+                if (cl[wd] >= 0) {
+                    xv[wd] = __ldg(x + cl[wd]);
+                    gr[wd] = __ldg(g + row);
+                }
+                rows_before += __popc(wds[wd]);
+            }
+#pragma unroll
+            for (int wd = 0; wd < MW; ++wd) {
+                if (cl[wd] >= 0) {
+                    const VT gg = scaled ? static_cast<VT>(a * gr[wd]) : gr[wd];
+                    gv[base + 32 * wd + lane] = gg * xv[wd];
+                }
+            }
         }
+    };
+    // Two sets of words and columns used in turn (no register copies, so no
+    // copy waits on a load still in flight): while one chunk is processed the
+    // next one's words and columns arrive in the other set.
+    struct Body {
+        ChunkDesc d;
+        uint32_t w[MW];
+        int32_t c[MW];
+    };
+    Body S0, S1;
+    S0.d = load_desc(c);
+    load_body(c, S0.d, S0.w, S0.c);
+    S1.d = load_desc(c + nw);
+    ChunkDesc d2 = load_desc(c + 2 * nw);
+    // P: chunk c (loaded), Q: chunk c + nw (descriptor only); afterwards P holds
+    // the descriptor of chunk c + 2nw
+    auto step = [&](Body &P, Body &Q) {
+        load_body(c + nw, Q.d, Q.w, Q.c);
+        const ChunkDesc d3 = load_desc(c + 3 * nw);
+        process(P.d, P.w, P.c);
+        P.d = d2;
+        d2 = d3;
+        c += nw;
+    };
+    while (c < n_chunks) {
+        step(S0, S1);
+        if (c >= n_chunks) break;
+        step(S1, S0);
     }
+}
+
+template <typename VT>
+static int grad_val_grid(int32_t n_chunks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grad_val_pipe<VT, kGradValWords>, 256, 0) !=
+            cudaSuccess ||
+        per_sm <= 0)
+        per_sm = 1;
+    const int64_t want = (static_cast<int64_t>(n_chunks) + 7) / 8;
+    const int64_t lim = static_cast<int64_t>(per_sm) * sms;
+    return static_cast<int>(want < lim ? want : lim);
 }
 
 cudaError_t launch_grad_val_chunks(const int32_t *rp, const int32_t *col, const void *chunks,
@@ -242,18 +299,16 @@ cudaError_t launch_grad_val_chunks(const int32_t *rp, const int32_t *col, const 
                                    const void *g, const void *x, double alpha, void *grad_val,
                                    cudaStream_t s) {
     if (n_chunks <= 0) return cudaSuccess;
-    const int grid = (n_chunks + 7) / 8;
+    if (mwp != kGradValWords) return cudaErrorInvalidValue;
     const ChunkDesc *c = static_cast<const ChunkDesc *>(chunks);
     if (vk == kF64)
-        k_grad_val_chunks<double><<<grid, 256, 0, s>>>(rp, col, c, masks, mwp, n_chunks,
-                                                       static_cast<const double *>(g),
-                                                       static_cast<const double *>(x), alpha,
-                                                       static_cast<double *>(grad_val));
+        k_grad_val_pipe<double, kGradValWords><<<grad_val_grid<double>(n_chunks), 256, 0, s>>>(
+            rp, col, c, masks, n_chunks, static_cast<const double *>(g), static_cast<const double *>(x), alpha,
+            static_cast<double *>(grad_val));
     else
-        k_grad_val_chunks<float><<<grid, 256, 0, s>>>(rp, col, c, masks, mwp, n_chunks,
-                                                      static_cast<const float *>(g),
-                                                      static_cast<const float *>(x), alpha,
-                                                      static_cast<float *>(grad_val));
+        k_grad_val_pipe<float, kGradValWords><<<grad_val_grid<float>(n_chunks), 256, 0, s>>>(
+            rp, col, c, masks, n_chunks, static_cast<const float *>(g), static_cast<const float *>(x), alpha,
+            static_cast<float *>(grad_val));
     return cudaGetLastError();
 }
 
