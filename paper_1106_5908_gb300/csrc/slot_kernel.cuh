@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         else return p.m;
     };
     const bool plain = (alpha == 1.0 && beta == 0.0);
+    const int emode = epi_mode(alpha, beta);
 
     auto regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
     auto hi_of = [&](const ChunkDesc &d) { return max(0, min(E, d.k1 - d.k0 - lane * E)); };
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
             rows_per_lane<VT, XT, YT, ACC, false>(m, r0, r1, x, y, alpha, beta, plain, lane);
         } else {
             RowEpilogue<YT> epi;
-            if constexpr (PRE) epi.prefetch(y, m.rmap, r0, r1 - r0, !plain && beta != 0.0, lane);
+            if constexpr (PRE) epi.prefetch(y, m.rmap, r0, r1 - r0, emode >= kEpiAdd, lane);
             const int hi = hi_of(dc);
             const uint32_t mbits = mc & ((1u << E) - 1u);
             if constexpr (kSlotScan<E, VT, PRE>::value) {
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
             }
             __syncwarp();
             if constexpr (PRE) {
-                epi.store(y, srow, r1 - r0, alpha, beta, plain, lane);
+                epi.store(y, srow, r1 - r0, alpha, beta, emode, lane);
             } else {
                 for (int q = lane; q < r1 - r0; q += 32)
                     store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);

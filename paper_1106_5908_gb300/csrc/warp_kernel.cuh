@@ -100,6 +100,16 @@ __device__ __forceinline__ void store_acc(YT *__restrict__ y, int64_t row, const
     store_row(y, row, a.get(), alpha, beta, plain, rmap);
 }
 
+// Form of the update y = alpha*v + beta*y, decided once per launch so that no
+// FP64 comparison or multiply by 1 runs per row: kEpiPlain y = v; kEpiScale
+// y = alpha*v; kEpiAdd y = v + y (alpha = beta = 1, as in the nonlocal part of
+// the split product); kEpiGeneral y = fma(alpha, v, beta*y).
+constexpr int kEpiPlain = 0, kEpiScale = 1, kEpiAdd = 2, kEpiGeneral = 3;
+__host__ __device__ __forceinline__ int epi_mode(double alpha, double beta) {
+    if (beta == 0.0) return alpha == 1.0 ? kEpiPlain : kEpiScale;
+    return (alpha == 1.0 && beta == 1.0) ? kEpiAdd : kEpiGeneral;
+}
+
 // Row epilogue of a regular chunk (at most kWarpRowCap rows, lane l owns rows
 // l, l+32, l+64): the output index of each row (through rmap) and, when beta is
 // nonzero, its old y value are loaded before the FMA chains run, so that their
@@ -126,22 +136,23 @@ struct RowEpilogue {
     }
     template <typename ACC>
     __device__ __forceinline__ void store(YT *__restrict__ y, const ACC *srow, int nrows, double alpha,
-                                          double beta, bool plain, int lane) const {
+                                          double beta, int mode, int lane) const {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int q = lane + 32 * k;
             if (q >= nrows) break;
             const ACC a = srow[q];
             if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
-                if (plain) {
+                if (mode == kEpiPlain) {
                     y[dst[k]] = a.h + a.l;
                     continue;
                 }
             }
             const double v = a.get();
             double out;
-            if (plain) out = v;
-            else if (beta == 0.0) out = alpha * v;
+            if (mode == kEpiPlain) out = v;
+            else if (mode == kEpiScale) out = alpha * v;
+            else if (mode == kEpiAdd) out = v + old[k];
             else out = fma(alpha, v, beta * old[k]);
             y[dst[k]] = narrow<YT>(out);
         }
