@@ -515,7 +515,8 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 //   (Hamiltonian-like 150.4 against 167.3 us): FP64 with E = 7 entries per lane
 //   for mean row lengths below 10 and E = 9 above (against the staged chunk
 //   kernels 150.6 vs 196.6 us; E = 11, 13, 15 lose to 9), FP32 storage with
-//   E = 7 (133 vs 138 us for E = 15, 152 us for the staged kernel).
+//   E = 9 (130.2 us; E = 7 133.5, E = 11 135.9, E = 15 138.1, the staged
+//   kernel 152 us).
 //   Otherwise: family 4 as above for FP64, the two-stage staged chunk kernel
 //   with E = 15 for FP32 storage.
 // The row-vector kernel's lanes per row T (family 1) is the power of two
@@ -534,7 +535,7 @@ void autotune(spmv_matrix *h) {
     h->sell_pad = h->n_rows > 0 ? sell_padding(h->h_rp.data(), h->n_rows, kSellSigma) : 1.0;
     if (h->vk == kF32) {
         h->family = scattered ? 4 : 0;
-        h->E = scattered ? 7 : 15;
+        h->E = scattered ? 9 : 15;
     } else {
         h->family = 4;
         h->E = (mean < 10.0) ? 7 : 9;
@@ -1175,7 +1176,7 @@ spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
     }
     if (family == 4) {
         if (param != 0 && param != 7 && param != 9 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
-        if (h->vk == kF32 && (param == 9 || param == 11)) return SPMV_ERR_INVALID_ARG;
+        if (h->vk == kF32 && param == 11) return SPMV_ERR_INVALID_ARG;
         h->family = 4;
         h->E = param ? param : (h->vk == kF32 ? 15 : 9);
         return SPMV_OK;

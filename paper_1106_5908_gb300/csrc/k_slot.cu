@@ -20,7 +20,8 @@ bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops) {
 
 bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     if (pre) {
-        // row-mapped products (the split's nonlocal part): FP64, E = 7
+        // row-mapped products (the split's nonlocal part): FP64, E = 7 (E = 9
+        // measured no faster there: split 230.9 against 229.4 us)
         if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64 && E == 7) {
             ops->launch = &SlotKernel<7, double, double, double, AccF64, true>::launch;
             return true;
@@ -37,6 +38,7 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     SPMV_S(kF64, kF64, kF64, kAccF64, 11, double, double, double, AccF64)
     SPMV_S(kF64, kF64, kF64, kAccF64, 15, double, double, double, AccF64)
     SPMV_S(kF32, kF32, kF32, kAccFF, 7, float, float, float, AccFF)
+    SPMV_S(kF32, kF32, kF32, kAccFF, 9, float, float, float, AccFF)
     SPMV_S(kF32, kF32, kF32, kAccFF, 15, float, float, float, AccFF)
 #undef SPMV_S
     return false;
