@@ -524,6 +524,11 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 constexpr int32_t kSellSigma = 4096;
 constexpr double kSellMaxPadding = 0.10;
 constexpr double kSellMinRowLength = 12.0;
+// batched slot-major launch: E = 9 from this mean row length on (else 7).  The
+// 256-matrix batch of 5-point Laplacians and Hamiltonian-like patterns (9.0
+// entries per row) takes 0.797 ms with E = 9 against 0.904 ms with 7 in FP64,
+// 0.605 against 0.645 ms with FP32 storage.
+constexpr double kBatchSlotMeanE9 = 8.0;
 
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
@@ -1696,10 +1701,12 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
         rows += mats[m]->n_rows;
     }
     b->E = (rows && static_cast<double>(nnz) / rows < 20.0) ? 7 : 15;
+    // slot-major entries per lane from the batch's mean row length, as for one matrix
+    const int ES = (rows && static_cast<double>(nnz) / rows < kBatchSlotMeanE9) ? 7 : 9;
     SlotOps sops;
-    if (slot_ops_batched(vk, acc, 7, &sops)) {
+    if (slot_ops_batched(vk, acc, ES, &sops)) {
         // the slot-major chunk kernel over one concatenated copy of all matrices
-        b->E = 7;
+        b->E = ES;
         b->use_slots = true;
         b->slot_off.assign(static_cast<size_t>(count) + 1, 0);
         b->vals_ver.assign(static_cast<size_t>(count), 0);
@@ -1708,12 +1715,12 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
         std::vector<int32_t> cm;
         for (int32_t m = 0; m < count; ++m) {
             b->slot_off[m] = static_cast<int32_t>(d.size());
-            make_slot_chunks(mats[m]->h_rp.data(), mats[m]->n_rows, 7, d, lm, &b->slots.n_long, &b->slots.n_empty);
+            make_slot_chunks(mats[m]->h_rp.data(), mats[m]->n_rows, ES, d, lm, &b->slots.n_long, &b->slots.n_empty);
             cm.resize(d.size(), m);
         }
         b->slot_off[count] = static_cast<int32_t>(d.size());
         b->slots.n = static_cast<int32_t>(d.size());
-        const size_t nslots = d.size() * 32 * 7;
+        const size_t nslots = d.size() * 32 * ES;
         const size_t vb = (vk == kF64) ? 8 : 4;
         bool ok = dmalloc(&b->slots.d, d.size()) == cudaSuccess && dmalloc(&b->slots.lmask, lm.size()) == cudaSuccess &&
                   dmalloc(&b->d_scmat, cm.size()) == cudaSuccess &&
@@ -1727,9 +1734,9 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
                                       cudaSuccess);
         for (int32_t m = 0; ok && m < count; ++m) {
             const int64_t off = b->slot_off[m], nch = b->slot_off[m + 1] - off;
-            ok = launch_slot_relayout(b->slots.d + off, 7, nch * 32 * 7, vk, mats[m]->d_val, mats[m]->d_col,
-                                      static_cast<char *>(b->slots.vals) + off * 32 * 7 * vb,
-                                      b->slots.cols + off * 32 * 7, nullptr) == cudaSuccess;
+            ok = launch_slot_relayout(b->slots.d + off, ES, nch * 32 * ES, vk, mats[m]->d_val, mats[m]->d_col,
+                                      static_cast<char *>(b->slots.vals) + off * 32 * ES * vb,
+                                      b->slots.cols + off * 32 * ES, nullptr) == cudaSuccess;
             b->vals_ver[m] = mats[m]->values_version;
         }
         ok = ok && cudaDeviceSynchronize() == cudaSuccess;
@@ -1823,12 +1830,12 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
         for (int32_t m = 0; m < b->count; ++m)
             if (b->mats[m]->values_version != b->vals_ver[m]) {
                 const int64_t off = b->slot_off[m], nch = b->slot_off[m + 1] - off;
-                CK(launch_slot_relayout(b->slots.d + off, 7, nch * 32 * 7, b->vk, b->mats[m]->d_val, nullptr,
-                                        static_cast<char *>(b->slots.vals) + off * 32 * 7 * vb, nullptr, s));
+                CK(launch_slot_relayout(b->slots.d + off, b->E, nch * 32 * b->E, b->vk, b->mats[m]->d_val, nullptr,
+                                        static_cast<char *>(b->slots.vals) + off * 32 * b->E * vb, nullptr, s));
                 b->vals_ver[m] = b->mats[m]->values_version;
             }
         SlotOps sops;
-        if (!slot_ops_batched(b->vk, acc, 7, &sops)) return SPMV_ERR_UNSUPPORTED;
+        if (!slot_ops_batched(b->vk, acc, b->E, &sops)) return SPMV_ERR_UNSUPPORTED;
         if (recapture) {
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }

@@ -11,8 +11,16 @@ bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops) {
         ops->launch = &SlotKernel<7, double, double, double, AccF64, false, true>::launch;
         return true;
     }
+    if (vk == kF64 && acc == kAccF64 && E == 9) {
+        ops->launch = &SlotKernel<9, double, double, double, AccF64, false, true>::launch;
+        return true;
+    }
     if (vk == kF32 && acc == kAccFF && E == 7) {
         ops->launch = &SlotKernel<7, float, float, float, AccFF, false, true>::launch;
+        return true;
+    }
+    if (vk == kF32 && acc == kAccFF && E == 9) {
+        ops->launch = &SlotKernel<9, float, float, float, AccFF, false, true>::launch;
         return true;
     }
     return false;
