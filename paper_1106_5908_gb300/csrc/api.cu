@@ -513,8 +513,10 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 //   Scattered columns: one row per lane gathers x from as many places as the
 //   slice has rows, so the slot-major chunk kernel (family 4) stays ahead
 //   (Hamiltonian-like 150.4 against 167.3 us): FP64 with E = 7 entries per lane
-//   for mean row lengths below 10 and E = 9 above (against the staged chunk
-//   kernels 150.6 vs 196.6 us; E = 11, 13, 15 lose to 9), FP32 storage with
+//   for mean row lengths below 8 and E = 9 above (against the staged chunk
+//   kernels 150.6 vs 196.6 us; E = 11, 13, 15 lose to 9; at 8.7 per row, the
+//   split's local part, E = 9 takes the one-stream split from 245.9 to 237.1 us;
+//   the 7-point matrix, 7 per row, keeps E = 7), FP32 storage with
 //   E = 9 (130.2 us; E = 7 133.5, E = 11 135.9, E = 15 138.1, the staged
 //   kernel 152 us).
 //   Otherwise: family 4 as above for FP64, the two-stage staged chunk kernel
@@ -543,7 +545,7 @@ void autotune(spmv_matrix *h) {
         h->E = scattered ? 9 : 15;
     } else {
         h->family = 4;
-        h->E = (mean < 10.0) ? 7 : 9;
+        h->E = (mean < 8.0) ? 7 : 9;
     }
     if (!scattered && mean >= kSellMinRowLength && h->sell_pad <= kSellMaxPadding) h->family = 5;
 }
@@ -1597,7 +1599,7 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
         if (!ind && !done) {
             // A^T's values in its own order: the slot-major kernel on a slot-major
             // copy of A^T (E by A^T's mean row length, as for a forward product)
-            const int ES = (h->vk == kF32) ? 15 : ((meanT < 10.0) ? 7 : 9);
+            const int ES = (h->vk == kF32) ? 15 : ((meanT < 8.0) ? 7 : 9);
             SlotOps sops;
             const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
             if (slot_ops(h->vk, h->vk, h->vk, acc, ES, false, &sops)) {
