@@ -157,6 +157,10 @@ def test_backward_27pt_fp32(c5):
     M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
     x = W.uniform(A.n_cols, W.SEED_C5_X).astype(np.float32)
     g = W.uniform(A.n_rows, W.SEED_C5_G).astype(np.float32)
+    # the forward product on the autotuned plan (row slices, float-float sums)
+    assert M.info()["family"] == 5
+    ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x.astype(np.float64), with_bound=True)
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "C5 fp32 forward")
     rgx, rgv, gbound = oracle.backward(A.row_ptr, A.col_idx, v32.astype(np.float64), A.n_cols,
                                        g.astype(np.float64), x.astype(np.float64), with_bound=True)
     for rep in range(2):

@@ -248,6 +248,26 @@ def test_fp32_widening_exact(acc, plan):
     assert np.array_equal(y[~nan], want[~nan]), np.flatnonzero(y[~nan] != want[~nan])[:8]
 
 
+@pytest.mark.parametrize("plan", [(5, 32), (5, 256), (5, 4096), (4, 9)])
+@pytest.mark.parametrize("shape", [(300, 200), (20000, 20000)])
+def test_fp32_storage_plans(plan, shape):
+    """FP32-stored values and vectors on the row-slice and slot-major kernels
+    (float-float sums): random rows with empty and long ones, every alpha/beta
+    form, against the oracle on the FP32 values at the FP32-storage bound."""
+    A = W.random_csr(*shape, seed=shape[0] + plan[1], max_len=40, long_rows=3, long_len=min(shape[1], 3000))
+    v32 = A.val.astype(np.float32)
+    M = make(W.CRS(A.row_ptr, A.col_idx, v32, A.n_cols))
+    M.set_plan(*plan)
+    x32 = W.uniform(A.n_cols, 7).astype(np.float32)
+    y32 = W.uniform(A.n_rows, 8).astype(np.float32)
+    for alpha, beta in [(1.0, 0.0), (-0.75, 1.0), (2.0, -0.5), (1.0, 1.0)]:
+        ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x32.astype(np.float64), alpha,
+                                 beta, y32.astype(np.float64), with_bound=True)
+        y = dev(y32)
+        M.apply(dev(x32), y, alpha, beta)
+        assert_within(host(y), ref, bound, 1e-6, f"fp32 {plan} a={alpha} b={beta}")
+
+
 @pytest.mark.parametrize("plan", [(4, 7), (4, 15), (5, 32), (5, 4096)])
 def test_slot_major_follows_new_values(plan):
     """The slot-major copies (plan families 4 and 5) are laid out again after new
