@@ -40,7 +40,7 @@ UNIT = "GB/s"
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
 TRAFFIC = {"kernel_hash": "9b7fdf6e19def671", "bytes_per_launch": 751066880,
-           "source": "profiles/k_slot_f64_hamiltonian_c2.md (mean of 3 launches)"}
+           "source": "profiles/k_slot_f64_hamiltonian_4194304.md (mean of 3 launches)"}
 
 
 def kernel_hash() -> str:
@@ -135,9 +135,9 @@ def whole_job_value(bytes_per_step: float, steps: int, world: int, max_ms: float
 
 # ------------------------------------------------------------------ workload
 
-def c2_workload():
-    A = W.hamiltonian_like(W.C2_N, seed=W.SEED_C2_MATRIX)
-    x = W.uniform(A.n_rows, W.SEED_C2_X)
+def hamiltonian_workload():
+    A = W.hamiltonian_like(W.HAMILTONIAN_N, seed=W.SEED_HAMILTONIAN)
+    x = W.uniform(A.n_rows, W.SEED_HAMILTONIAN_X)
     return A, x
 
 
@@ -160,7 +160,7 @@ def run_reference(args, rank):
     import oracle
     if rank != 0:
         return
-    A, x = c2_workload()
+    A, x = hamiltonian_workload()
     n, nnz = A.n_rows, A.nnz
     bs = oracle.split_blocks(A.row_ptr, 8)
     cnt, _, _, _ = oracle.split_halo(A.row_ptr, A.col_idx, A.n_cols, bs)
@@ -226,7 +226,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build_lib()
     dev = torch.device("cuda", local_rank)
-    A, x = c2_workload()
+    A, x = hamiltonian_workload()
     n, nnz = A.n_rows, A.nnz
     M64 = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
     M32 = Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols)
@@ -515,9 +515,9 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
             "time_per_rhs_vs_plain": ms / nrhs / form_ms["plain"]}
         del X, Y
     try:  # IR-CG on the 3D 7-point Poisson matrix
-        A3 = W.laplace3d(W.C3_GRID)
+        A3 = W.laplace3d(W.POISSON7_GRID)
         M3 = Matrix.from_csr(A3.row_ptr, A3.col_idx, A3.val, A3.n_cols)
-        b = torch.as_tensor(W.uniform(A3.n_rows, W.SEED_C3_B)).to(dev)
+        b = torch.as_tensor(W.uniform(A3.n_rows, W.SEED_POISSON7_B)).to(dev)
         x3 = torch.rand(A3.n_rows, dtype=torch.float64, device=dev)
         y3 = torch.empty_like(x3)
         ms_plain3 = _time(lambda: M3.apply(x3, y3), 10)
@@ -541,10 +541,10 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
     except Exception as e:  # reported, not hidden
         out["ir_cg_poisson160"] = {"error": repr(e)}
     try:  # reverse pass on the 27-point pattern
-        A5 = W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
+        A5 = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
         M5 = Matrix.from_csr(A5.row_ptr, A5.col_idx, A5.val, A5.n_cols)
-        x5 = torch.as_tensor(W.uniform(A5.n_cols, W.SEED_C5_X)).to(dev)
-        g5 = torch.as_tensor(W.uniform(A5.n_rows, W.SEED_C5_G)).to(dev)
+        x5 = torch.as_tensor(W.uniform(A5.n_cols, W.SEED_STENCIL27_X)).to(dev)
+        g5 = torch.as_tensor(W.uniform(A5.n_rows, W.SEED_STENCIL27_G)).to(dev)
         y5 = torch.empty_like(g5)
         ms_f = _time(lambda: M5.apply(x5, y5), 10)
         M5.backward(g5, x5)
@@ -566,7 +566,7 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
     except Exception as e:
         out["backward_27pt128"] = {"error": repr(e)}
     try:  # 256 uneven matrices, one persistent launch replayed from a CUDA graph
-        sizes = W.batch_sizes(W.C4_COUNT)
+        sizes = W.batch_sizes(W.BATCH_COUNT)
         mats, xs, ys, b_tot, nnz_tot = [], [], [], 0, 0
         for m, n in enumerate(sizes):
             Am = W.batch_matrix(m, int(n))
@@ -599,13 +599,13 @@ def run_only_plain(args, local_rank):
     torch.cuda.set_device(local_rank)
     build_lib()
     if args.only == "plain":
-        A, x = c2_workload()
+        A, x = hamiltonian_workload()
     elif args.only == "poisson7":
-        A = W.laplace3d(W.C3_GRID)
-        x = W.uniform(A.n_cols, W.SEED_C3_B)
+        A = W.laplace3d(W.POISSON7_GRID)
+        x = W.uniform(A.n_cols, W.SEED_POISSON7_B)
     else:
-        A = W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
-        x = W.uniform(A.n_cols, W.SEED_C5_X)
+        A = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
+        x = W.uniform(A.n_cols, W.SEED_STENCIL27_X)
     M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
     xd = torch.as_tensor(x).cuda()
     y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
@@ -636,7 +636,7 @@ def run_ordering_study(args, local_rank):
     from paper_1106_5908_gb300.build import build as build_lib
     torch.cuda.set_device(local_rank)
     build_lib()
-    A, x = c2_workload()
+    A, x = hamiltonian_workload()
     # per-row tolerance scale sum_j |a_ij x_j| of the natural order
     scale = np.add.reduceat(np.abs(A.val) * np.abs(x[A.col_idx]), A.row_ptr[:-1].astype(np.int64))
     y_nat = None

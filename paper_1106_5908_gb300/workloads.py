@@ -21,16 +21,16 @@ from dataclasses import dataclass
 import numpy as np
 
 # Fixed seeds of the synthetic workloads.
-SEED_C1_X = 1101
-SEED_C1_XINT = 1102
-SEED_C2_MATRIX = 2201
-SEED_C2_X = 2202
-SEED_C3_B = 3301
-SEED_C4_X = 4401
-SEED_C4_BATCH = 4402
-SEED_C5_VAL = 5501
-SEED_C5_X = 5502
-SEED_C5_G = 5503
+SEED_LAPLACE2D_X = 1101
+SEED_LAPLACE2D_XINT = 1102
+SEED_HAMILTONIAN = 2201
+SEED_HAMILTONIAN_X = 2202
+SEED_POISSON7_B = 3301
+SEED_BLOCK_X = 4401
+SEED_BATCH = 4402
+SEED_STENCIL27_VAL = 5501
+SEED_STENCIL27_X = 5502
+SEED_STENCIL27_G = 5503
 
 
 @dataclass
@@ -116,7 +116,7 @@ def laplace3d(n: int) -> CRS:
     return _stencil((n, n, n), _sorted_offsets(3, offs), 6.0, -1.0)
 
 
-def stencil27(n: int, seed: int = SEED_C5_VAL) -> CRS:
+def stencil27(n: int, seed: int = SEED_STENCIL27_VAL) -> CRS:
     """27-point pattern on an n^3 grid (diagonal included), values N(0,1), not
     symmetric."""
     offs = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
@@ -146,7 +146,7 @@ def _distinct_draw(rng, avail, counts, kmax):
     return np.where(srt == big, -1, srt)
 
 
-def hamiltonian_like(n: int, seed: int = SEED_C2_MATRIX, band: int = 64,
+def hamiltonian_like(n: int, seed: int = SEED_HAMILTONIAN, band: int = 64,
                      mean_len: float = 6.0, min_len: int = 2, max_len: int = 16) -> CRS:
     """Symmetric Hamiltonian-like matrix (stand-in for HMeP).
 
@@ -248,12 +248,12 @@ def truncated_laplace2d(n: int) -> CRS:
     return CRS(_row_ptr_from_counts(counts), cols[keep].astype(np.int32), vals[keep], n)
 
 
-def batch_sizes(count: int = 256, seed: int = SEED_C4_BATCH, lo: int = 1000, hi: int = 200000):
+def batch_sizes(count: int = 256, seed: int = SEED_BATCH, lo: int = 1000, hi: int = 200000):
     rng = np.random.default_rng(seed)
     return rng.integers(lo, hi + 1, count)
 
 
-def batch_matrix(m: int, n: int, seed: int = SEED_C4_BATCH) -> CRS:
+def batch_matrix(m: int, n: int, seed: int = SEED_BATCH) -> CRS:
     """Matrix m of the uneven batch: even m a truncated 2D 5-point Laplacian, odd m
     a Hamiltonian-like pattern, both of order n."""
     if m % 2 == 0:
@@ -296,10 +296,10 @@ def bandwidth(A: CRS) -> int:
 
 
 # Shapes of the five synthetic configurations.
-C1_GRID = 256          # 2D 5-point, N = 65,536
-C2_N = 4_194_304       # Hamiltonian-like, N = 4,194,304
-C3_GRID = 160          # 3D 7-point, N = 4,096,000
-C4_NRHS = (1, 4, 8, 16, 32)
-C4_COUNT = 256
-C5_GRID = 128          # 3D 27-point, N = 2,097,152
-C5_FD_GRID = 16
+LAPLACE2D_GRID = 256          # 2D 5-point, N = 65,536
+HAMILTONIAN_N = 4_194_304       # Hamiltonian-like, N = 4,194,304
+POISSON7_GRID = 160          # 3D 7-point, N = 4,096,000
+BLOCK_NRHS = (1, 4, 8, 16, 32)
+BATCH_COUNT = 256
+STENCIL27_GRID = 128          # 3D 27-point, N = 2,097,152
+STENCIL27_FD_GRID = 16

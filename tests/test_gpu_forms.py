@@ -129,55 +129,55 @@ def test_backward_after_new_values(kind):
 
 
 @pytest.fixture(scope="module")
-def c5():
-    return W.stencil27(W.C5_GRID, seed=W.SEED_C5_VAL)
+def st27():
+    return W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
 
 
-def test_backward_27pt_128(c5):
-    A = c5
+def test_backward_27pt_128(st27):
+    A = st27
     assert (A.n_rows, A.nnz) == (2097152, 55742968)
     M = make(A)
-    x = W.uniform(A.n_cols, W.SEED_C5_X)
-    g = W.uniform(A.n_rows, W.SEED_C5_G)
+    x = W.uniform(A.n_cols, W.SEED_STENCIL27_X)
+    g = W.uniform(A.n_rows, W.SEED_STENCIL27_G)
     ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
-    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C5 forward")
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "27-point forward")
     rgx, rgv, gbound = oracle.backward(*A.astuple(), A.n_cols, g, x, with_bound=True)
     # the first reverse pass reads A^T's values through the permutation; the
     # second lays them out once and runs the row-slice kernel on A^T
     for rep in range(2):
         gx, gv = M.backward(dev(g), dev(x))
-        assert_within(host(gx), rgx, gbound, 1e-13, f"C5 grad_x pass {rep}")
-        assert_bitexact(host(gv), rgv, f"C5 grad_val pass {rep}")
+        assert_within(host(gx), rgx, gbound, 1e-13, f"27-point grad_x pass {rep}")
+        assert_bitexact(host(gv), rgv, f"27-point grad_val pass {rep}")
 
 
-def test_backward_27pt_fp32(c5):
+def test_backward_27pt_fp32(st27):
     from paper_1106_5908_gb300 import Matrix
-    A = c5
+    A = st27
     v32 = A.val.astype(np.float32)
     M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
-    x = W.uniform(A.n_cols, W.SEED_C5_X).astype(np.float32)
-    g = W.uniform(A.n_rows, W.SEED_C5_G).astype(np.float32)
+    x = W.uniform(A.n_cols, W.SEED_STENCIL27_X).astype(np.float32)
+    g = W.uniform(A.n_rows, W.SEED_STENCIL27_G).astype(np.float32)
     # the forward product on the autotuned plan (row slices, float-float sums)
     assert M.info()["family"] == 5
     ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x.astype(np.float64), with_bound=True)
-    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "C5 fp32 forward")
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "27-point fp32 forward")
     rgx, rgv, gbound = oracle.backward(A.row_ptr, A.col_idx, v32.astype(np.float64), A.n_cols,
                                        g.astype(np.float64), x.astype(np.float64), with_bound=True)
     for rep in range(2):
         gx, gv = M.backward(dev(g), dev(x))
-        assert_within(host(gx), rgx, gbound, 1e-6, f"C5 fp32 grad_x pass {rep}")
-        assert_within(host(gv), rgv, np.abs(rgv), 1e-6, f"C5 fp32 grad_val pass {rep}")
+        assert_within(host(gx), rgx, gbound, 1e-6, f"27-point fp32 grad_x pass {rep}")
+        assert_within(host(gv), rgv, np.abs(rgv), 1e-6, f"27-point fp32 grad_val pass {rep}")
 
 
 def test_autograd_fd_16cubed():
     """SpMVFunction against central differences (torch.autograd.gradcheck) and
     against the oracle's reverse pass on the 16^3 27-point instance."""
     from paper_1106_5908_gb300 import spmv
-    A = W.stencil27(W.C5_FD_GRID, seed=W.SEED_C5_VAL)
+    A = W.stencil27(W.STENCIL27_FD_GRID, seed=W.SEED_STENCIL27_VAL)
     M = make(A)
     val = dev(A.val).requires_grad_(True)
-    x = dev(W.uniform(A.n_cols, W.SEED_C5_X)).requires_grad_(True)
-    g = W.uniform(A.n_rows, W.SEED_C5_G)
+    x = dev(W.uniform(A.n_cols, W.SEED_STENCIL27_X)).requires_grad_(True)
+    g = W.uniform(A.n_rows, W.SEED_STENCIL27_G)
     y = spmv(M, val, x, 1.25)
     y.backward(dev(g))
     rgx, rgv = oracle.backward(*A.astuple(), A.n_cols, g, host(x), 1.25)
@@ -202,13 +202,13 @@ def test_autograd_fd_16cubed():
 
 # ---------------------------------------------------------------- solvers
 
-@pytest.mark.parametrize("grid", [24, W.C3_GRID])
+@pytest.mark.parametrize("grid", [24, W.POISSON7_GRID])
 @pytest.mark.parametrize("inner", [(1e-3, 500), (1e-4, 200)])
 def test_ir_cg_and_cg(grid, inner):
     from paper_1106_5908_gb300 import cg, ir_cg
     A = W.laplace3d(grid)
     M = make(A)
-    b = W.uniform(A.n_rows, W.SEED_C3_B)
+    b = W.uniform(A.n_rows, W.SEED_POISSON7_B)
     bd = dev(b)
     x, st = ir_cg(M, bd, outer_tol=1e-12, max_outer=50, inner_tol=inner[0], max_inner=inner[1])
     assert st["converged"], st
@@ -278,7 +278,7 @@ def test_batched_256_full_size():
     persistent launch replayed from a CUDA graph; every result against the
     oracle, for two right-hand sides (the second replay reuses the graph)."""
     from paper_1106_5908_gb300 import Batch, Matrix
-    sizes = W.batch_sizes(W.C4_COUNT)
+    sizes = W.batch_sizes(W.BATCH_COUNT)
     As, mats = [], []
     for m, n in enumerate(sizes):
         A = W.batch_matrix(m, int(n))

@@ -14,53 +14,53 @@ torch = pytest.importorskip("torch")
 
 
 @pytest.fixture(scope="module")
-def c2():
+def ham():
     need_gpu()
-    A = W.hamiltonian_like(W.C2_N, seed=W.SEED_C2_MATRIX)
-    x = W.uniform(A.n_rows, W.SEED_C2_X)
+    A = W.hamiltonian_like(W.HAMILTONIAN_N, seed=W.SEED_HAMILTONIAN)
+    x = W.uniform(A.n_rows, W.SEED_HAMILTONIAN_X)
     ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
     return A, x, ref, bound
 
 
 @pytest.fixture(scope="module")
-def m2(c2):
+def m_ham(ham):
     from paper_1106_5908_gb300 import Matrix
-    A = c2[0]
+    A = ham[0]
     return Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
 
 
-def test_c2_shape(c2):
-    A = c2[0]
+def test_hamiltonian_shape(ham):
+    A = ham[0]
     assert A.n_rows == 4194304
     assert 12.5 < A.nnz / A.n_rows < 13.5
 
 
-def test_c2_plain_f64(c2, m2):
-    A, x, ref, bound = c2
-    y = m2.apply(dev(x))
-    assert_within(host(y), ref, bound, 1e-13, "C2 plain")
+def test_hamiltonian_plain_f64(ham, m_ham):
+    A, x, ref, bound = ham
+    y = m_ham.apply(dev(x))
+    assert_within(host(y), ref, bound, 1e-13, "Hamiltonian plain")
     # alpha/beta update on the same launch shape
     y0 = W.uniform(A.n_rows, 77)
     ref2, bound2 = oracle.spmv(*A.astuple(), x, -2.0, 0.5, y0, with_bound=True)
     y = dev(y0)
-    m2.apply(dev(x), y, -2.0, 0.5)
-    assert_within(host(y), ref2, bound2, 1e-13, "C2 alpha/beta")
+    m_ham.apply(dev(x), y, -2.0, 0.5)
+    assert_within(host(y), ref2, bound2, 1e-13, "Hamiltonian alpha/beta")
 
 
 @pytest.mark.parametrize("plan", [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 256),
                                   (5, 4096), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 2)])
-def test_c2_plans(c2, m2, plan):
-    A, x, ref, bound = c2
-    m2.set_plan(*plan)
+def test_hamiltonian_plans(ham, m_ham, plan):
+    A, x, ref, bound = ham
+    m_ham.set_plan(*plan)
     try:
-        assert_within(host(m2.apply(dev(x))), ref, bound, 1e-13, f"C2 plan={plan}")
+        assert_within(host(m_ham.apply(dev(x))), ref, bound, 1e-13, f"Hamiltonian plan={plan}")
     finally:
-        m2.set_plan(0, 16)
+        m_ham.set_plan(0, 16)
 
 
-def test_c2_split(c2, m2):
-    A, x, ref, bound = c2
-    sp = m2.split(8)
+def test_hamiltonian_split(ham, m_ham):
+    A, x, ref, bound = ham
+    sp = m_ham.split(8)
     plan = sp.plan()
     bs = oracle.split_blocks(A.row_ptr, 8)
     assert_bitexact(plan["block_start"], bs, "block starts")
@@ -86,11 +86,11 @@ def test_c2_split(c2, m2):
 
 
 @pytest.mark.parametrize("equal_rows", [False, True])
-def test_c2_split_vector_mode(c2, m2, equal_rows):
+def test_hamiltonian_split_vector_mode(ham, m_ham, equal_rows):
     """Vector mode (Fig. kernel_schemes (a)) gives the plain product; equal-rows
     blocks start at floor(b*n/8)."""
-    A, x, ref, bound = c2
-    sp = m2.split(8, equal_rows=equal_rows)
+    A, x, ref, bound = ham
+    sp = m_ham.split(8, equal_rows=equal_rows)
     plan = sp.plan()
     if equal_rows:
         assert_bitexact(plan["block_start"], np.array([b * A.n_rows // 8 for b in range(9)]), "equal rows")
@@ -149,24 +149,24 @@ def test_split_explicit_blocks_small():
 
 
 @pytest.mark.parametrize("acc", ["ff", "f64"])
-def test_c2_fp32_storage(c2, acc):
+def test_hamiltonian_fp32_storage(ham, acc):
     from paper_1106_5908_gb300 import Matrix
-    A, x, _, _ = c2
+    A, x, _, _ = ham
     v32 = A.val.astype(np.float32)
     x32 = x.astype(np.float32)
     M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
     M.set_accumulator(acc)
     ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x32.astype(np.float64),
                              with_bound=True)
-    assert_within(host(M.apply(dev(x32))), ref, bound, 1e-6, f"C2 fp32 y32 {acc}")
-    assert_within(host(M.apply(dev(x32), out_dtype=torch.float64)), ref, bound, 1e-6, f"C2 fp32 y64 {acc}")
+    assert_within(host(M.apply(dev(x32))), ref, bound, 1e-6, f"Hamiltonian fp32 y32 {acc}")
+    assert_within(host(M.apply(dev(x32), out_dtype=torch.float64)), ref, bound, 1e-6, f"Hamiltonian fp32 y64 {acc}")
 
 
 @pytest.mark.parametrize("nrhs", [4, 8, 16, 32])
-def test_c2_block_vectors(c2, m2, nrhs):
-    A, _, _, _ = c2
-    X = W.uniform(0, W.SEED_C4_X, shape=(A.n_rows, nrhs))
-    Y = host(m2.spmm(dev(X)))
+def test_hamiltonian_block_vectors(ham, m_ham, nrhs):
+    A, _, _, _ = ham
+    X = W.uniform(0, W.SEED_BLOCK_X, shape=(A.n_rows, nrhs))
+    Y = host(m_ham.spmm(dev(X)))
     rng = np.random.default_rng(nrhs)
     rows = np.sort(rng.choice(A.n_rows, 4000, replace=False))
     # oracle on the sampled rows (a sub-CRS with the same entries)
@@ -175,4 +175,4 @@ def test_c2_block_vectors(c2, m2, nrhs):
     np.cumsum(lens, out=rp[1:])
     idx = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1]) for r in rows])
     ref, bound = oracle.spmm(rp.astype(np.int32), A.col_idx[idx], A.val[idx], X, with_bound=True)
-    assert_within(Y[rows].ravel(), ref.ravel(), bound.ravel(), 1e-13, f"C2 nrhs={nrhs}")
+    assert_within(Y[rows].ravel(), ref.ravel(), bound.ravel(), 1e-13, f"Hamiltonian nrhs={nrhs}")

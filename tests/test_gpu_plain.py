@@ -129,31 +129,31 @@ def test_histogram_matches_oracle():
 
 @pytest.mark.parametrize("plan", [(0, 16), (0, 8), (2, 15), (1, 4)])
 def test_laplace2d_256(plan):
-    A = W.laplace2d(W.C1_GRID)
+    A = W.laplace2d(W.LAPLACE2D_GRID)
     assert (A.n_rows, A.nnz) == (65536, 326656)
     M = make(A)
     M.set_plan(*plan)
-    x = W.uniform(A.n_rows, W.SEED_C1_X)
+    x = W.uniform(A.n_rows, W.SEED_LAPLACE2D_X)
     ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
-    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C1 uniform")
-    xi = W.integers(A.n_rows, W.SEED_C1_XINT)
-    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "C1 integer")
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "5-point 256^2 uniform")
+    xi = W.integers(A.n_rows, W.SEED_LAPLACE2D_XINT)
+    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "5-point 256^2 integer")
 
 
 @pytest.fixture(scope="module")
-def c3():
-    return W.laplace3d(W.C3_GRID)
+def poisson7():
+    return W.laplace3d(W.POISSON7_GRID)
 
 
-def test_laplace3d_160(c3):
-    A = c3
+def test_laplace3d_160(poisson7):
+    A = poisson7
     assert (A.n_rows, A.nnz) == (4096000, 28518400)
     M = make(A)
-    x = W.uniform(A.n_rows, W.SEED_C3_B)
+    x = W.uniform(A.n_rows, W.SEED_POISSON7_B)
     ref, bound = oracle.spmv(*A.astuple(), x, with_bound=True)
-    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "C3 FP64")
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-13, "7-point 160^3 FP64")
     xi = W.integers(A.n_rows, 7)
-    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "C3 integer")
+    assert_bitexact(host(M.apply(dev(xi))), oracle.spmv(*A.astuple(), xi), "7-point 160^3 integer")
 
 
 @pytest.mark.parametrize("acc", ["ff", "f64"])
@@ -184,12 +184,12 @@ def test_fp32_storage_integer_bitexact():
     assert_bitexact(host(M.apply(dev(x), out_dtype=torch.float64)), ref, "fp32->f64 integer")
 
 
-def test_laplace3d_160_fp32(c3):
-    A = c3
+def test_laplace3d_160_fp32(poisson7):
+    A = poisson7
     M = make(W.CRS(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols))
-    x = W.uniform(A.n_rows, W.SEED_C3_B).astype(np.float32)
+    x = W.uniform(A.n_rows, W.SEED_POISSON7_B).astype(np.float32)
     ref, bound = oracle.spmv(*A.astuple(), x.astype(np.float64), with_bound=True)
-    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "C3 FP32")
+    assert_within(host(M.apply(dev(x))), ref, bound, 1e-6, "7-point 160^3 FP32")
 
 
 def test_autotuner_choices():

@@ -249,9 +249,9 @@ def test_backward_vs_dense_and_fd(seed):
 
 
 def test_fd_on_27pt_16cubed():
-    A = W.stencil27(W.C5_FD_GRID, seed=W.SEED_C5_VAL)
-    x = W.uniform(A.n_cols, W.SEED_C5_X)
-    g = W.uniform(A.n_rows, W.SEED_C5_G)
+    A = W.stencil27(W.STENCIL27_FD_GRID, seed=W.SEED_STENCIL27_VAL)
+    x = W.uniform(A.n_cols, W.SEED_STENCIL27_X)
+    g = W.uniform(A.n_rows, W.SEED_STENCIL27_G)
     gx, gv = oracle.backward(*A.astuple(), A.n_cols, g, x)
     rng = np.random.default_rng(0)
     h = 1e-3

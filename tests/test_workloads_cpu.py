@@ -1,5 +1,5 @@
 """The input generators' structural helpers: the orderings of the ordering study
-(P A P^T against a dense permutation, RCM on a scrambled stencil) and the C2
+(P A P^T against a dense permutation, RCM on a scrambled stencil) and the Hamiltonian-like
 recipe's shape."""
 import numpy as np
 import pytest
