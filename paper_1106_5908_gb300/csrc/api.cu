@@ -1578,9 +1578,10 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
             if (h->sell_padT < 0.0) h->sell_padT = sell_padding(h->h_rowT.data(), h->n_cols, kSellSigma);
             SellOps lops;
             const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
-            if (h->sell_padT <= kSellMaxPadding && sell_ops(h->vk, h->vk, h->vk, acc, &lops)) {
-                SellTable *t = get_sell(h, kSellSigma, s, true);
-                if (!t) return SPMV_ERR_ALLOC;
+            SellTable *t = nullptr;
+            // without its copy (allocation failed) the slot-major path below runs
+            if (h->sell_padT <= kSellMaxPadding && sell_ops(h->vk, h->vk, h->vk, acc, &lops) &&
+                (t = get_sell(h, kSellSigma, s, true)) != nullptr) {
                 SellParams lp{};
                 lp.slices = t->d;
                 lp.srows = t->srows;
