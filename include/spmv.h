@@ -215,7 +215,12 @@ spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X,
  *                 transposed CRS built once on the device and kept in the handle;
  *   grad_val[k] = alpha * g[row(k)] * x[col_idx[k]]   (nnz entries, CRS order).
  * Both outputs are overwritten; either may be NULL.  FP64 handles take FP64 g,
- * x and outputs; FP32-storage handles take FP32 g, x and write FP32 outputs. */
+ * x and outputs; FP32-storage handles take FP32 g, x and write FP32 outputs.
+ * The first call after new values reads A^T's values through the permutation;
+ * the second lays them out in A^T order once (kept until spmv_set_values) and
+ * from then on grad_x runs on a copy of A^T (row slices for stencil-like
+ * matrices with at least 12 entries per row, slot-major otherwise).  Results are
+ * unchanged up to summation order. */
 spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void *x,
                           void *grad_x, void *grad_val, void *stream);
 
