@@ -11,7 +11,10 @@ module only marshals numpy arrays.  Each function names the passage it follows.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against
 dense or brute-force references, closed forms, invariants or the paper's printed
-numbers; none is "parity unpinned".
+numbers; the timed node-level forms (``spmv_omp``, ``spmv_f32``, ``spmv_split``,
+``Node``) are pinned bit for bit against the plain loop (or against a literal
+Python statement of the split), at every thread count tested; none is "parity
+unpinned".
 """
 from __future__ import annotations
 
@@ -31,6 +34,7 @@ _lib = None
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -56,8 +60,28 @@ def _load():
     vp = ctypes.c_void_p
     lib.oracle_spmv.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p, vp]
     lib.oracle_spmv.restype = None
-    lib.oracle_spmv_omp.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p]
+    lib.oracle_spmv_omp.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p, i32]
     lib.oracle_spmv_omp.restype = None
+    lib.oracle_thread_rows.argtypes = [i32, _i32p, i32, _i32p]
+    lib.oracle_thread_rows.restype = None
+    lib.oracle_spmv_f32.argtypes = [i32, _i32p, _i32p, _f32p, _f32p, f64, f64, _f32p, i32]
+    lib.oracle_spmv_f32.restype = None
+    lib.oracle_spmv_split.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p, i32, _i32p, _i32p,
+                                      _i32p, _f64p]
+    lib.oracle_spmv_split.restype = None
+    lib.oracle_node_create.argtypes = [i32, i32, _i32p, _i32p, _f64p, _f64p, i32, i32, _i32p, _i32p, _i32p]
+    lib.oracle_node_create.restype = vp
+    lib.oracle_node_destroy.argtypes = [vp]
+    lib.oracle_node_destroy.restype = None
+    for f in ("oracle_node_spmv", "oracle_node_spmv_f32", "oracle_node_spmv_split"):
+        getattr(lib, f).argtypes = [vp, f64, f64]
+        getattr(lib, f).restype = None
+    lib.oracle_node_set_y.argtypes = [vp, vp, vp]
+    lib.oracle_node_set_y.restype = None
+    lib.oracle_node_get_y.argtypes = [vp, vp, vp]
+    lib.oracle_node_get_y.restype = None
+    lib.oracle_node_threads.argtypes = [vp]
+    lib.oracle_node_threads.restype = i32
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_spmm.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, f64, f64, _f64p, vp]
@@ -118,12 +142,138 @@ def spmv(row_ptr, col_idx, val, x, alpha=1.0, beta=0.0, y=None, with_bound=False
     return out[:n]
 
 
-def spmv_omp(row_ptr, col_idx, val, x, y_out, alpha=1.0, beta=0.0):
-    """Sect. 2 node-level variant (OpenMP over rows), writing into ``y_out``; for the
-    timed CPU baseline.  Returns the thread count used."""
+def thread_rows(row_ptr, nthreads):
+    """Sect. 3.5 explicit work distribution: the T+1 bounds of the contiguous,
+    nonzero-balanced row chunk of each thread."""
     lib = _load()
-    lib.oracle_spmv_omp(y_out.size, row_ptr, col_idx, val, x, float(alpha), float(beta), y_out)
-    return lib.oracle_num_threads()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    out = np.zeros(int(nthreads) + 1, np.int32)
+    lib.oracle_thread_rows(rp.size - 1, rp, int(nthreads), out)
+    return out
+
+
+def spmv_omp(row_ptr, col_idx, val, x, y_out, alpha=1.0, beta=0.0, nthreads=0):
+    """Sect. 2 node-level loop with the Sect. 3.5 work distribution (one contiguous
+    nonzero-balanced row chunk per thread), writing into ``y_out`` (FP64, n_rows;
+    read when beta != 0).  ``nthreads`` <= 0 uses every available thread.  Returns
+    the thread count used."""
+    lib = _load()
+    rp, ci, v = _crs(row_ptr, col_idx, val)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    if xx.size == 0:
+        xx = np.zeros(1, np.float64)
+    assert y_out.dtype == np.float64 and y_out.flags["C_CONTIGUOUS"] and y_out.size >= rp.size - 1
+    T = int(nthreads) if nthreads and nthreads > 0 else lib.oracle_num_threads()
+    yy = y_out if y_out.size > 0 else np.zeros(1, np.float64)
+    lib.oracle_spmv_omp(rp.size - 1, rp, ci, v, xx, float(alpha), float(beta), yy, T)
+    return T
+
+
+def spmv_f32(row_ptr, col_idx, val32, x32, alpha=1.0, beta=0.0, y=None, nthreads=1):
+    """FP32-stored values and vectors with FP64 accumulation: exact FP64 products
+    of the floats, FP64 row sums in increasing k, one rounding of
+    alpha*acc + beta*y to float.  Returns y (float32)."""
+    lib = _load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(val32, dtype=np.float32)
+    xx = np.ascontiguousarray(x32, dtype=np.float32)
+    if ci.size == 0:
+        ci = np.zeros(1, np.int32)
+    if v.size == 0:
+        v = np.zeros(1, np.float32)
+    if xx.size == 0:
+        xx = np.zeros(1, np.float32)
+    n = rp.size - 1
+    out = np.zeros(max(n, 1), np.float32)
+    if y is not None and beta != 0.0:
+        out[:n] = np.asarray(y, dtype=np.float32)
+    lib.oracle_spmv_f32(n, rp, ci, v, xx, float(alpha), float(beta), out, int(nthreads))
+    return out[:n]
+
+
+def spmv_split(row_ptr, col_idx, val, x, n_cols, block_start, alpha=1.0, beta=0.0, y=None):
+    """Sect. 3.4 split form over the row blocks ``block_start`` (Sect. 3.2): halo
+    gather, local part (with beta), then the nonlocal part added onto y for rows
+    with nonlocal entries.  Returns y (FP64)."""
+    lib = _load()
+    rp, ci, v = _crs(row_ptr, col_idx, val)
+    n = rp.size - 1
+    bs = np.ascontiguousarray(block_start, dtype=np.int32)
+    cnt, hmap, _, _ = split_halo(rp, ci, n_cols, bs)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    if xx.size == 0:
+        xx = np.zeros(1, np.float64)
+    out = np.zeros(max(n, 1), np.float64)
+    if y is not None and beta != 0.0:
+        out[:n] = np.asarray(y, dtype=np.float64)
+    hm = np.ascontiguousarray(hmap if hmap.size else np.zeros(1, np.int32), dtype=np.int32)
+    halo = np.zeros(max(hmap.size, 1), np.float64)
+    lib.oracle_spmv_split(n, rp, ci, v, xx, float(alpha), float(beta), out, bs.size - 1, bs,
+                          np.ascontiguousarray(cnt, dtype=np.int32), hm, halo)
+    return out[:n]
+
+
+class Node:
+    """The node-level CPU code of Sect. 2 and 3.5 for timing: the matrix, its FP32
+    copies and its split form over ``nblocks`` nonzero-balanced row blocks, copied
+    into memory first touched by the thread that computes with it, one contiguous
+    nonzero-balanced row chunk per thread.  ``spmv``, ``spmv_f32`` and
+    ``spmv_split`` run on the node's own vectors (``y``/``y32`` read back with
+    ``get_y``)."""
+
+    def __init__(self, row_ptr, col_idx, val, x, n_cols, nthreads=0, nblocks=8):
+        lib = _load()
+        rp, ci, v = _crs(row_ptr, col_idx, val)
+        n = rp.size - 1
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        if xx.size == 0:
+            xx = np.zeros(1, np.float64)
+        nblocks = max(1, int(nblocks))
+        bs = split_blocks(rp, nblocks)
+        cnt, hmap, _, _ = split_halo(rp, ci, n_cols, bs)
+        hm = np.ascontiguousarray(hmap if hmap.size else np.zeros(1, np.int32), dtype=np.int32)
+        self.block_start = bs
+        self.total_halo = int(cnt.sum())
+        self.n_rows = n
+        self._lib = lib
+        self._h = lib.oracle_node_create(n, int(n_cols), rp, ci, v, xx, int(nthreads), nblocks, bs,
+                                         np.ascontiguousarray(cnt, dtype=np.int32), hm)
+
+    @property
+    def threads(self) -> int:
+        return int(self._lib.oracle_node_threads(self._h))
+
+    def spmv(self, alpha=1.0, beta=0.0):
+        self._lib.oracle_node_spmv(self._h, float(alpha), float(beta))
+
+    def spmv_f32(self, alpha=1.0, beta=0.0):
+        self._lib.oracle_node_spmv_f32(self._h, float(alpha), float(beta))
+
+    def spmv_split(self, alpha=1.0, beta=0.0):
+        self._lib.oracle_node_spmv_split(self._h, float(alpha), float(beta))
+
+    def set_y(self, y=None, y32=None):
+        a = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
+        b = None if y32 is None else np.ascontiguousarray(y32, dtype=np.float32)
+        self._lib.oracle_node_set_y(self._h, _ptr(a), _ptr(b))
+
+    def get_y(self):
+        y = np.zeros(max(self.n_rows, 1), np.float64)
+        y32 = np.zeros(max(self.n_rows, 1), np.float32)
+        self._lib.oracle_node_get_y(self._h, _ptr(y), _ptr(y32))
+        return y[: self.n_rows], y32[: self.n_rows]
+
+    def close(self):
+        if self._h:
+            self._lib.oracle_node_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def num_threads() -> int:

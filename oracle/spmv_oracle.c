@@ -51,15 +51,52 @@ void oracle_spmv(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
     }
 }
 
-/* The node-level parallelisation of Sect. 2: the outer (row) loop of Listing 1
- * split statically across OpenMP threads.  Same arithmetic per row as oracle_spmv.
- * Used only as the timed CPU baseline. */
-void oracle_spmv_omp(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
-                     const double *val, const double *x, double alpha, double beta,
-                     double *y)
+/* Thread chunks of the explicit work distribution of Sect. 3.5: one contiguous,
+ * nonzero-balanced range of rows per thread.  Thread t of T starts at the first
+ * row whose starting offset is at least ceil(t*nnz/T) (the block rule of
+ * Sect. 3.2 applied to threads); thread 0 starts at row 0 and the last thread
+ * ends at n_rows.  bounds receives T+1 row indices. */
+static int32_t first_row_at(int32_t n_rows, const int32_t *row_ptr, int64_t target)
 {
-#pragma omp parallel for schedule(static)
-    for (int32_t i = 0; i < n_rows; ++i) {
+    int32_t lo = 0, hi = n_rows;
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (row_ptr[mid] < target)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+void oracle_thread_rows(int32_t n_rows, const int32_t *row_ptr, int32_t nthreads, int32_t *bounds)
+{
+    int64_t nnz = row_ptr[n_rows];
+    bounds[0] = 0;
+    for (int32_t t = 1; t < nthreads; ++t)
+        bounds[t] = first_row_at(n_rows, row_ptr, ((int64_t)t * nnz + nthreads - 1) / nthreads);
+    bounds[nthreads] = n_rows;
+}
+
+int oracle_num_threads(void);
+
+static int32_t threads_or_max(int32_t nthreads)
+{
+    return nthreads > 0 ? nthreads : oracle_num_threads();
+}
+
+#ifdef _OPENMP
+#define THREAD_ID() omp_get_thread_num()
+#else
+#define THREAD_ID() 0
+#endif
+
+/* Listing 1's row loop over rows [lo, hi), generalised to alpha/beta, with the
+ * arithmetic of oracle_spmv (no magnitude sum). */
+static void spmv_rows(int32_t lo, int32_t hi, const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *val, const double *x, double alpha, double beta, double *y)
+{
+    for (int32_t i = lo; i < hi; ++i) {
         double acc = 0.0;
         for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
             acc = acc + val[k] * x[col_idx[k]];
@@ -68,6 +105,403 @@ void oracle_spmv_omp(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_
         else
             y[i] = alpha * acc + beta * y[i];
     }
+}
+
+/* The node-level parallelisation of Sect. 2 (the outer row loop of Listing 1
+ * split across OpenMP threads) with the explicit work distribution of Sect. 3.5:
+ * thread t computes the rows of oracle_thread_rows' chunk t.  nthreads <= 0 means
+ * every available thread; 1 is the single-thread loop.  Same per-row arithmetic
+ * as oracle_spmv, so the result does not depend on the thread count.  The
+ * arrays are used where the caller placed them (see oracle_node_* for the
+ * first-touch placement). */
+void oracle_spmv_omp(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                     const double *val, const double *x, double alpha, double beta,
+                     double *y, int32_t nthreads)
+{
+    int32_t T = threads_or_max(nthreads);
+    int32_t *bounds = (int32_t *)malloc(sizeof(int32_t) * ((size_t)T + 1));
+    oracle_thread_rows(n_rows, row_ptr, T, bounds);
+#pragma omp parallel num_threads(T)
+    {
+        int32_t t = THREAD_ID();
+        spmv_rows(bounds[t], bounds[t + 1], row_ptr, col_idx, val, x, alpha, beta, y);
+    }
+    free(bounds);
+}
+
+/* FP32-stored values and vectors with FP64 accumulation (the precision form of
+ * the library, not in the paper): each product of two floats is formed exactly
+ * in FP64, the row sum runs in FP64 in increasing k, and y_i = alpha*acc +
+ * beta*y_i is rounded once to float.  Thread chunks as oracle_spmv_omp. */
+void oracle_spmv_f32(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                     const float *val, const float *x, double alpha, double beta,
+                     float *y, int32_t nthreads)
+{
+    int32_t T = threads_or_max(nthreads);
+    int32_t *bounds = (int32_t *)malloc(sizeof(int32_t) * ((size_t)T + 1));
+    oracle_thread_rows(n_rows, row_ptr, T, bounds);
+#pragma omp parallel num_threads(T)
+    {
+        int32_t t = THREAD_ID();
+        for (int32_t i = bounds[t]; i < bounds[t + 1]; ++i) {
+            double acc = 0.0;
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
+                acc = acc + (double)val[k] * (double)x[col_idx[k]];
+            double out;
+            if (beta == 0.0)
+                out = alpha * acc;
+            else
+                out = alpha * acc + beta * (double)y[i];
+            y[i] = (float)out;
+        }
+    }
+    free(bounds);
+}
+
+/* Position of column j in the sorted list map[0..count), or -1. */
+static int32_t find_sorted(const int32_t *map, int32_t count, int32_t j)
+{
+    int32_t lo = 0, hi = count;
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (map[mid] < j)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < count && map[lo] == j) ? lo : -1;
+}
+
+/* The local/nonlocal split of one multiplication (Sect. 3.4), over the row
+ * blocks of Sect. 3.2 (block_start: nblocks+1 row indices; halo_count and
+ * halo_map as oracle_split_halo writes them).  For each block b with rows
+ * [s_b, s_{b+1}):
+ *   1. halo[h] = x[map_b[h]] (the nonlocal right-hand side elements it receives);
+ *   2. local part:    y_i = alpha*sum_{local k} val[k]*x[col[k]] (+ beta*y_i),
+ *                     k increasing, a column being local iff it lies in [s_b, s_{b+1});
+ *   3. nonlocal part: y_i = y_i + alpha*sum_{nonlocal k} val[k]*halo[pos(col[k])],
+ *                     k increasing, for rows with at least one nonlocal entry
+ *                     (y is written a second time, the extra traffic of Eq. 2).
+ * pos() is the binary search of the column in the block's sorted map.  halo is a
+ * work array of the total halo length. */
+void oracle_spmv_split(int32_t n_rows, const int32_t *row_ptr, const int32_t *col_idx,
+                       const double *val, const double *x, double alpha, double beta,
+                       double *y, int32_t nblocks, const int32_t *block_start,
+                       const int32_t *halo_count, const int32_t *halo_map, double *halo)
+{
+    int64_t off = 0;
+    (void)n_rows;
+    for (int32_t b = 0; b < nblocks; ++b) {
+        int32_t lo = block_start[b], hi = block_start[b + 1];
+        const int32_t *map = halo_map + off;
+        double *hb = halo + off;
+        for (int32_t h = 0; h < halo_count[b]; ++h)
+            hb[h] = x[map[h]];
+        for (int32_t i = lo; i < hi; ++i) {
+            double acc = 0.0;
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col_idx[k];
+                if (j >= lo && j < hi)
+                    acc = acc + val[k] * x[j];
+            }
+            if (beta == 0.0)
+                y[i] = alpha * acc;
+            else
+                y[i] = alpha * acc + beta * y[i];
+        }
+        for (int32_t i = lo; i < hi; ++i) {
+            double acc = 0.0;
+            int32_t any = 0;
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col_idx[k];
+                if (!(j >= lo && j < hi)) {
+                    acc = acc + val[k] * hb[find_sorted(map, halo_count[b], j)];
+                    any = 1;
+                }
+            }
+            if (any)
+                y[i] = y[i] + alpha * acc;
+        }
+        off += halo_count[b];
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * The node-level CPU code as the paper runs it (Sect. 2 and 3.5), for timing:
+ * every array the multiplication touches is copied into memory that is first
+ * touched by the thread that later computes with it (NUMA-aware placement by
+ * first touch), and each thread owns one contiguous, nonzero-balanced chunk of
+ * rows (oracle_thread_rows).  The node holds the FP64 matrix and vectors, the
+ * FP32-stored copies of values and vectors, and the split form over nblocks row
+ * blocks (local and nonlocal entries of each row stored apart, nonlocal columns
+ * replaced once by their position in the concatenated halo buffer: the
+ * bookkeeping of Sect. 3.2, done once).  Every product is the same arithmetic as
+ * oracle_spmv (plain), oracle_spmv_f32 (FP32 storage) and oracle_spmv_split
+ * (split form), row by row.
+ * ------------------------------------------------------------------------- */
+typedef struct oracle_node {
+    int32_t n_rows, n_cols, T, nblocks;
+    int32_t *bounds;                  /* T+1 thread chunk bounds */
+    int32_t *rp, *ci;                 /* CRS */
+    double *val, *x, *y;
+    float *val32, *x32, *y32;
+    /* split form */
+    int32_t *blk_lo, *blk_hi;         /* block of each row: [lo, hi) */
+    int32_t *rpl, *cil, *rpn, *cin;   /* local / nonlocal CRS (cin: halo positions) */
+    double *vall, *valn;
+    int32_t *hmap;                    /* concatenated halo maps */
+    double *halo;
+    int64_t total_halo;
+    int32_t *hbounds;                 /* T+1 chunk bounds of the halo gather */
+} oracle_node;
+
+static void *alloc_untouched(size_t bytes)
+{
+    void *p = NULL;
+    if (bytes == 0)
+        bytes = 64;
+    if (posix_memalign(&p, 64, bytes) != 0)
+        return NULL;
+    return p;
+}
+
+void oracle_node_destroy(oracle_node *nd);
+
+oracle_node *oracle_node_create(int32_t n_rows, int32_t n_cols, const int32_t *row_ptr,
+                                const int32_t *col_idx, const double *val, const double *x,
+                                int32_t nthreads, int32_t nblocks, const int32_t *block_start,
+                                const int32_t *halo_count, const int32_t *halo_map)
+{
+    oracle_node *nd = (oracle_node *)calloc(1, sizeof(oracle_node));
+    int64_t nnz = row_ptr[n_rows];
+    nd->n_rows = n_rows;
+    nd->n_cols = n_cols;
+    nd->T = threads_or_max(nthreads);
+    nd->nblocks = nblocks;
+    nd->bounds = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nd->T + 1));
+    oracle_thread_rows(n_rows, row_ptr, nd->T, nd->bounds);
+    nd->rp = (int32_t *)alloc_untouched(sizeof(int32_t) * ((size_t)n_rows + 1));
+    nd->ci = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)nnz);
+    nd->val = (double *)alloc_untouched(sizeof(double) * (size_t)nnz);
+    nd->val32 = (float *)alloc_untouched(sizeof(float) * (size_t)nnz);
+    nd->x = (double *)alloc_untouched(sizeof(double) * (size_t)n_cols);
+    nd->x32 = (float *)alloc_untouched(sizeof(float) * (size_t)n_cols);
+    nd->y = (double *)alloc_untouched(sizeof(double) * (size_t)n_rows);
+    nd->y32 = (float *)alloc_untouched(sizeof(float) * (size_t)n_rows);
+    /* split bookkeeping on one thread (once), into staging arrays */
+    int32_t *cnt_l = (int32_t *)calloc((size_t)n_rows + 1, sizeof(int32_t));
+    int32_t *cnt_n = (int32_t *)calloc((size_t)n_rows + 1, sizeof(int32_t));
+    int32_t *blo = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n_rows + 1));
+    int32_t *bhi = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n_rows + 1));
+    int64_t *hoff = (int64_t *)calloc((size_t)nblocks + 1, sizeof(int64_t));
+    for (int32_t b = 0; b < nblocks; ++b)
+        hoff[b + 1] = hoff[b] + halo_count[b];
+    nd->total_halo = nblocks > 0 ? hoff[nblocks] : 0;
+    for (int32_t b = 0; b < nblocks; ++b)
+        for (int32_t i = block_start[b]; i < block_start[b + 1]; ++i) {
+            blo[i] = block_start[b];
+            bhi[i] = block_start[b + 1];
+        }
+    for (int32_t i = 0; i < n_rows; ++i)
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int32_t j = col_idx[k];
+            if (j >= blo[i] && j < bhi[i])
+                cnt_l[i + 1] += 1;
+            else
+                cnt_n[i + 1] += 1;
+        }
+    for (int32_t i = 0; i < n_rows; ++i) {
+        cnt_l[i + 1] += cnt_l[i];
+        cnt_n[i + 1] += cnt_n[i];
+    }
+    int64_t nl = cnt_l[n_rows], nn = cnt_n[n_rows];
+    int32_t *s_cil = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nl + 1));
+    int32_t *s_cin = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nn + 1));
+    double *s_vall = (double *)malloc(sizeof(double) * ((size_t)nl + 1));
+    double *s_valn = (double *)malloc(sizeof(double) * ((size_t)nn + 1));
+    for (int32_t b = 0; b < nblocks; ++b)
+        for (int32_t i = block_start[b]; i < block_start[b + 1]; ++i) {
+            int32_t pl = cnt_l[i], pn = cnt_n[i];
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col_idx[k];
+                if (j >= blo[i] && j < bhi[i]) {
+                    s_cil[pl] = j;
+                    s_vall[pl++] = val[k];
+                } else {
+                    s_cin[pn] = (int32_t)(hoff[b] + find_sorted(halo_map + hoff[b], halo_count[b], j));
+                    s_valn[pn++] = val[k];
+                }
+            }
+        }
+    nd->blk_lo = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)n_rows);
+    nd->blk_hi = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)n_rows);
+    nd->rpl = (int32_t *)alloc_untouched(sizeof(int32_t) * ((size_t)n_rows + 1));
+    nd->rpn = (int32_t *)alloc_untouched(sizeof(int32_t) * ((size_t)n_rows + 1));
+    nd->cil = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)nl);
+    nd->cin = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)nn);
+    nd->vall = (double *)alloc_untouched(sizeof(double) * (size_t)nl);
+    nd->valn = (double *)alloc_untouched(sizeof(double) * (size_t)nn);
+    nd->hmap = (int32_t *)alloc_untouched(sizeof(int32_t) * (size_t)nd->total_halo);
+    nd->halo = (double *)alloc_untouched(sizeof(double) * (size_t)nd->total_halo);
+    nd->hbounds = (int32_t *)malloc(sizeof(int32_t) * ((size_t)nd->T + 1));
+    for (int32_t t = 0; t <= nd->T; ++t)
+        nd->hbounds[t] = (int32_t)(nd->total_halo * t / nd->T);
+    /* first touch: each thread writes the parts it computes with */
+#pragma omp parallel num_threads(nd->T)
+    {
+        int32_t t = THREAD_ID();
+        int32_t lo = nd->bounds[t], hi = nd->bounds[t + 1];
+        for (int32_t i = lo; i < hi; ++i) {
+            nd->rp[i] = row_ptr[i];
+            nd->rpl[i] = cnt_l[i];
+            nd->rpn[i] = cnt_n[i];
+            nd->blk_lo[i] = blo[i];
+            nd->blk_hi[i] = bhi[i];
+            nd->y[i] = 0.0;
+            nd->y32[i] = 0.0f;
+        }
+        if (t == nd->T - 1) {
+            nd->rp[n_rows] = row_ptr[n_rows];
+            nd->rpl[n_rows] = cnt_l[n_rows];
+            nd->rpn[n_rows] = cnt_n[n_rows];
+        }
+        for (int64_t k = row_ptr[lo]; k < row_ptr[hi]; ++k) {
+            nd->ci[k] = col_idx[k];
+            nd->val[k] = val[k];
+            nd->val32[k] = (float)val[k];
+        }
+        for (int64_t k = cnt_l[lo]; k < cnt_l[hi]; ++k) {
+            nd->cil[k] = s_cil[k];
+            nd->vall[k] = s_vall[k];
+        }
+        for (int64_t k = cnt_n[lo]; k < cnt_n[hi]; ++k) {
+            nd->cin[k] = s_cin[k];
+            nd->valn[k] = s_valn[k];
+        }
+        /* x is distributed like the rows (Sect. 3.2); columns past n_rows go
+         * to the last thread */
+        int32_t xlo = lo < n_cols ? lo : n_cols, xhi = hi < n_cols ? hi : n_cols;
+        if (t == nd->T - 1)
+            xhi = n_cols;
+        for (int32_t j = xlo; j < xhi; ++j) {
+            nd->x[j] = x[j];
+            nd->x32[j] = (float)x[j];
+        }
+        for (int32_t h = nd->hbounds[t]; h < nd->hbounds[t + 1]; ++h) {
+            nd->hmap[h] = halo_map[h];
+            nd->halo[h] = 0.0;
+        }
+    }
+    free(cnt_l);
+    free(cnt_n);
+    free(blo);
+    free(bhi);
+    free(hoff);
+    free(s_cil);
+    free(s_cin);
+    free(s_vall);
+    free(s_valn);
+    return nd;
+}
+
+void oracle_node_destroy(oracle_node *nd)
+{
+    if (!nd)
+        return;
+    free(nd->bounds); free(nd->rp); free(nd->ci); free(nd->val); free(nd->x); free(nd->y);
+    free(nd->val32); free(nd->x32); free(nd->y32);
+    free(nd->blk_lo); free(nd->blk_hi); free(nd->rpl); free(nd->cil); free(nd->rpn); free(nd->cin);
+    free(nd->vall); free(nd->valn); free(nd->hmap); free(nd->halo); free(nd->hbounds);
+    free(nd);
+}
+
+/* y = alpha*A*x + beta*y on the node's own arrays (plain FP64). */
+void oracle_node_spmv(oracle_node *nd, double alpha, double beta)
+{
+#pragma omp parallel num_threads(nd->T)
+    {
+        int32_t t = THREAD_ID();
+        spmv_rows(nd->bounds[t], nd->bounds[t + 1], nd->rp, nd->ci, nd->val, nd->x, alpha, beta, nd->y);
+    }
+}
+
+/* The FP32-storage product on the node's float copies (arithmetic of
+ * oracle_spmv_f32). */
+void oracle_node_spmv_f32(oracle_node *nd, double alpha, double beta)
+{
+#pragma omp parallel num_threads(nd->T)
+    {
+        int32_t t = THREAD_ID();
+        for (int32_t i = nd->bounds[t]; i < nd->bounds[t + 1]; ++i) {
+            double acc = 0.0;
+            for (int32_t k = nd->rp[i]; k < nd->rp[i + 1]; ++k)
+                acc = acc + (double)nd->val32[k] * (double)nd->x32[nd->ci[k]];
+            double out;
+            if (beta == 0.0)
+                out = alpha * acc;
+            else
+                out = alpha * acc + beta * (double)nd->y32[i];
+            nd->y32[i] = (float)out;
+        }
+    }
+}
+
+/* The split form on the node (arithmetic of oracle_spmv_split): halo gather,
+ * then the local part of every row, then the nonlocal part of every row that has
+ * nonlocal entries; each thread on its own chunk, with a barrier between the
+ * steps (the halo must be complete before any nonlocal part runs). */
+void oracle_node_spmv_split(oracle_node *nd, double alpha, double beta)
+{
+#pragma omp parallel num_threads(nd->T)
+    {
+        int32_t t = THREAD_ID();
+        for (int32_t h = nd->hbounds[t]; h < nd->hbounds[t + 1]; ++h)
+            nd->halo[h] = nd->x[nd->hmap[h]];
+        int32_t lo = nd->bounds[t], hi = nd->bounds[t + 1];
+        for (int32_t i = lo; i < hi; ++i) {
+            double acc = 0.0;
+            for (int32_t k = nd->rpl[i]; k < nd->rpl[i + 1]; ++k)
+                acc = acc + nd->vall[k] * nd->x[nd->cil[k]];
+            if (beta == 0.0)
+                nd->y[i] = alpha * acc;
+            else
+                nd->y[i] = alpha * acc + beta * nd->y[i];
+        }
+#pragma omp barrier
+        for (int32_t i = lo; i < hi; ++i) {
+            if (nd->rpn[i + 1] == nd->rpn[i])
+                continue;
+            double acc = 0.0;
+            for (int32_t k = nd->rpn[i]; k < nd->rpn[i + 1]; ++k)
+                acc = acc + nd->valn[k] * nd->halo[nd->cin[k]];
+            nd->y[i] = nd->y[i] + alpha * acc;
+        }
+    }
+}
+
+void oracle_node_set_y(oracle_node *nd, const double *y, const float *y32)
+{
+    for (int32_t i = 0; i < nd->n_rows; ++i) {
+        if (y)
+            nd->y[i] = y[i];
+        if (y32)
+            nd->y32[i] = y32[i];
+    }
+}
+
+void oracle_node_get_y(const oracle_node *nd, double *y, float *y32)
+{
+    for (int32_t i = 0; i < nd->n_rows; ++i) {
+        if (y)
+            y[i] = nd->y[i];
+        if (y32)
+            y32[i] = nd->y32[i];
+    }
+}
+
+int32_t oracle_node_threads(const oracle_node *nd)
+{
+    return nd->T;
 }
 
 int oracle_num_threads(void)

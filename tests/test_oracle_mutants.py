@@ -11,11 +11,14 @@ import tempfile
 import pytest
 
 import oracle
+import test_oracle_node_pins as npins
 import test_oracle_pins as pins
 
 FUNCS = ("oracle_spmv", "oracle_spmv_omp", "oracle_num_threads", "oracle_spmm", "oracle_transpose",
          "oracle_backward", "oracle_split_blocks", "oracle_split_halo", "oracle_cg",
-         "oracle_row_histogram")
+         "oracle_row_histogram", "oracle_thread_rows", "oracle_spmv_f32", "oracle_spmv_split",
+         "oracle_node_create", "oracle_node_destroy", "oracle_node_spmv", "oracle_node_spmv_f32",
+         "oracle_node_spmv_split", "oracle_node_set_y", "oracle_node_get_y", "oracle_node_threads")
 
 
 @contextlib.contextmanager
@@ -49,6 +52,21 @@ SPMV_PINS = [
     lambda: pins.test_integer_exact(1),
     lambda: pins.test_empty_rows_give_beta_y(),
     lambda: pins.test_one_based_listing_reading(),
+]
+
+OMP_PINS = [
+    lambda: npins.test_spmv_omp_equals_plain_bit_for_bit((17, 33), 3),
+    lambda: npins.test_spmv_omp_equals_plain_bit_for_bit((301, 301), 0),
+    lambda: npins.test_spmv_omp_hamiltonian_like(3),
+    lambda: npins.test_thread_rows_is_the_nonzero_balanced_rule(4, 1),
+]
+NODE_PINS = [
+    lambda: npins.test_first_touch_node_equals_the_plain_forms((301, 301), 3, 8),
+    lambda: npins.test_first_touch_node_hamiltonian_like(),
+]
+SPLIT_PINS = [
+    lambda: npins.test_spmv_split_literal_and_plain((64, 64), 3),
+    lambda: npins.test_spmv_split_integer_exact(),
 ]
 
 MUTANTS = {
@@ -92,6 +110,31 @@ MUTANTS = {
     "halo keeps local columns": ("if (j >= lo && j < hi) {\n                    ++nl;",
                                  "if (j >= lo && j < hi) {\n                    used[j] = 1;\n                    ++nl;",
                                  [lambda: pins.test_split_halo_brute_force(4)]),
+    # node-level loop (Sect. 2 / 3.5 explicit distribution)
+    "node-level loop drops the last entry of each row": (
+        "for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)\n            acc = acc + val[k] * x[col_idx[k]];",
+        "for (int32_t k = row_ptr[i]; k < row_ptr[i + 1] - 1; ++k)\n            acc = acc + val[k] * x[col_idx[k]];",
+        OMP_PINS),
+    "node-level loop drops beta": ("y[i] = alpha * acc + beta * y[i];", "y[i] = alpha * acc + y[i];", OMP_PINS),
+    "thread chunk skips its first row": ("spmv_rows(bounds[t], bounds[t + 1], row_ptr",
+                                         "spmv_rows(bounds[t] + (t > 0), bounds[t + 1], row_ptr", OMP_PINS),
+    "thread chunks round the nonzero target down": ("((int64_t)t * nnz + nthreads - 1) / nthreads",
+                                                    "((int64_t)t * nnz) / nthreads", OMP_PINS),
+    "FP32 form sums in float": ("acc = acc + (double)val[k] * (double)x[col_idx[k]];",
+                                "acc = (float)(acc + (float)((float)val[k] * (float)x[col_idx[k]]));",
+                                [lambda: npins.test_spmv_f32_is_the_upcast_product_rounded_once((200, 150), 1)]),
+    "first-touch copy forgets the last row offset": ("nd->rp[n_rows] = row_ptr[n_rows];", "(void)0;", NODE_PINS),
+    "node FP32 form reads the FP64 values": ("acc = acc + (double)nd->val32[k] * (double)nd->x32[nd->ci[k]];",
+                                             "acc = acc + nd->val[k] * nd->x[nd->ci[k]];", NODE_PINS),
+    # split form (Sect. 3.4)
+    "split nonlocal part applies beta again": ("y[i] = y[i] + alpha * acc;", "y[i] = beta * y[i] + alpha * acc;",
+                                               SPLIT_PINS),
+    "split local test includes the block end": ("if (j >= lo && j < hi)\n                    acc = acc + val[k] * x[j];",
+                                                "if (j >= lo && j <= hi)\n                    acc = acc + val[k] * x[j];",
+                                                SPLIT_PINS),
+    "node split reads the halo one position off": ("acc = acc + nd->valn[k] * nd->halo[nd->cin[k]];",
+                                                   "acc = acc + nd->valn[k] * nd->halo[nd->cin[k] > 0 ? nd->cin[k] - 1 : 0];",
+                                                   NODE_PINS),
     # CG
     "CG update with the wrong sign": ("r[i] = r[i] - a * q[i];", "r[i] = r[i] + a * q[i];",
                                       [lambda: pins.test_cg_solves_spd()]),
