@@ -36,6 +36,12 @@ from paper_1106_5908_gb300 import workloads as W  # noqa: E402
 METRIC = "spMVM GB/s & GFLOP/s vs 8 TB/s HBM roofline; FP32-IR/block/adjoint vs plain FP64"
 UNIT = "GB/s"
 
+# Throughput of FP64 FMAs on this GPU, measured once by a microbenchmark kernel
+# (8 independent chains x 64 warps per SM, CUDA events): the second ceiling of the
+# forms that issue more FP64 instructions per byte (block vectors, reverse pass,
+# FP32 storage with FP64 accumulation).
+FP64_FMA_PER_S = 598e9
+
 # DRAM traffic of one launch of the plain FP64 chunk kernel on this workload, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
@@ -470,6 +476,11 @@ def consistency_check(y64, ys, y32):
     return out
 
 
+def fp64_frac(fp64_ops, ms):
+    """FP64 instructions (lane operations) per second over the measured FMA rate."""
+    return fp64_ops / (ms / 1e3) / FP64_FMA_PER_S
+
+
 def _time(fn, reps):
     import torch
     fn()
@@ -523,8 +534,21 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
         out[f"block_nrhs{nrhs}"] = {
             "ms": ms, "GBs": model.bytes_spmm(A.n_rows, A.n_cols, A.nnz, nrhs) / ms / 1e6,
             "GFLOPs": model.flops(A.nnz, nrhs) / ms / 1e6,
-            "time_per_rhs_vs_plain": ms / nrhs / form_ms["plain"]}
+            "time_per_rhs_vs_plain": ms / nrhs / form_ms["plain"],
+            "fp64_pipe_frac": fp64_frac(A.nnz * nrhs, ms)}
         del X, Y
+    try:  # FP32 storage with the FP64-FMA accumulator (one FP64 FMA per entry)
+        M32a = Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(np.float32), A.n_cols)
+        M32a.set_accumulator("f64")
+        x32 = torch.as_tensor(x).to(dev).float()
+        y32 = torch.empty(A.n_rows, dtype=torch.float32, device=dev)
+        ms = _time(lambda: M32a.apply(x32, y32), 10)
+        b32 = model.bytes_plain(A.n_rows, A.n_cols, A.nnz, val_bytes=4, x_bytes=4, y_bytes=4)
+        out["fp32_storage_fp64_fma"] = {"ms": ms, "GBs": b32 / ms / 1e6, "time_vs_plain": ms / form_ms["plain"],
+                                        "fp64_pipe_frac": fp64_frac(A.nnz, ms), "plan": M32a.info()}
+        del M32a, x32, y32
+    except Exception as e:  # reported, not hidden
+        out["fp32_storage_fp64_fma"] = {"error": repr(e)}
     try:  # IR-CG on the 3D 7-point Poisson matrix
         A3 = W.laplace3d(W.POISSON7_GRID)
         M3 = Matrix.from_csr(A3.row_ptr, A3.col_idx, A3.val, A3.n_cols)
@@ -548,51 +572,60 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
         del M3, b, x3, y3, xi, xc
     except Exception as e:  # reported, not hidden
         out["ir_cg_poisson160"] = {"error": repr(e)}
-    try:  # reverse pass on the 27-point pattern
-        A5 = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
-        M5 = Matrix.from_csr(A5.row_ptr, A5.col_idx, A5.val, A5.n_cols)
-        x5 = torch.as_tensor(W.uniform(A5.n_cols, W.SEED_STENCIL27_X)).to(dev)
-        g5 = torch.as_tensor(W.uniform(A5.n_rows, W.SEED_STENCIL27_G)).to(dev)
-        y5 = torch.empty_like(g5)
-        ms_f = _time(lambda: M5.apply(x5, y5), 10)
-        M5.backward(g5, x5)
-        ms_b = _time(lambda: M5.backward(g5, x5), 10)
-        ms_gx = _time(lambda: M5.backward(g5, x5, need_val=False), 10)
-        # after new values the transposed values are laid out again (one
-        # permutation pass): time set_values + backward minus set_values alone
-        v5 = torch.as_tensor(A5.val).to(dev)
-        ms_sv = _time(lambda: M5.set_values(v5), 10)
-        ms_svb = _time(lambda: (M5.set_values(v5), M5.backward(g5, x5)), 10)
-        out["backward_27pt128"] = {
-            "forward_ms": ms_f, "backward_ms": ms_b, "grad_x_ms": ms_gx,
-            "backward_after_new_values_ms": ms_svb - ms_sv,
-            "forward_GBs": model.bytes_plain(A5.n_rows, A5.n_cols, A5.nnz) / ms_f / 1e6,
-            "backward_GBs": model.bytes_backward(A5.n_rows, A5.n_cols, A5.nnz) / ms_b / 1e6,
-            "time_vs_plain": ms_b / ms_f}
-        del v5
-        del M5, x5, g5, y5
-    except Exception as e:
-        out["backward_27pt128"] = {"error": repr(e)}
-    try:  # 256 uneven matrices, one persistent launch replayed from a CUDA graph
-        sizes = W.batch_sizes(W.BATCH_COUNT)
-        mats, xs, ys, b_tot, nnz_tot = [], [], [], 0, 0
-        for m, n in enumerate(sizes):
-            Am = W.batch_matrix(m, int(n))
-            mats.append(Matrix.from_csr(Am.row_ptr, Am.col_idx, Am.val, Am.n_cols))
-            xs.append(torch.rand(Am.n_cols, dtype=torch.float64, device=dev))
-            ys.append(torch.empty(Am.n_rows, dtype=torch.float64, device=dev))
-            b_tot += model.bytes_plain(Am.n_rows, Am.n_cols, Am.nnz)
-            nnz_tot += Am.nnz
-        B = Batch(mats)
-        ms_b = _time(lambda: B.apply(xs, ys), 10)
-        ms_each = _time(lambda: [M.apply(xx, yy) for M, xx, yy in zip(mats, xs, ys)], 3)
-        out["batched_256"] = {
-            "ms": ms_b, "GBs": b_tot / ms_b / 1e6, "GFLOPs": 2 * nnz_tot / ms_b / 1e6,
-            "nnz": nnz_tot, "separate_launches_ms": ms_each,
-            "GBs_vs_plain": (b_tot / ms_b) / (b_plain / form_ms["plain"]), "plan": B.info()}
-        del B, mats, xs, ys
-    except Exception as e:
-        out["batched_256"] = {"error": repr(e)}
+    A5 = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
+    for label, npdt in (("backward_27pt128", np.float64), ("backward_27pt128_f32", np.float32)):
+        try:  # reverse pass on the 27-point pattern, FP64 and FP32 storage
+            vb = 8 if npdt == np.float64 else 4
+            M5 = Matrix.from_csr(A5.row_ptr, A5.col_idx, A5.val.astype(npdt), A5.n_cols)
+            x5 = torch.as_tensor(W.uniform(A5.n_cols, W.SEED_STENCIL27_X).astype(npdt)).to(dev)
+            g5 = torch.as_tensor(W.uniform(A5.n_rows, W.SEED_STENCIL27_G).astype(npdt)).to(dev)
+            y5 = torch.empty_like(g5)
+            ms_f = _time(lambda: M5.apply(x5, y5), 10)
+            M5.backward(g5, x5)
+            ms_b = _time(lambda: M5.backward(g5, x5), 10)
+            ms_gx = _time(lambda: M5.backward(g5, x5, need_val=False), 10)
+            # after new values the transposed values are laid out again (one
+            # permutation pass): time set_values + backward minus set_values alone
+            v5 = torch.as_tensor(A5.val.astype(npdt)).to(dev)
+            ms_sv = _time(lambda: M5.set_values(v5), 10)
+            ms_svb = _time(lambda: (M5.set_values(v5), M5.backward(g5, x5)), 10)
+            bf = model.bytes_plain(A5.n_rows, A5.n_cols, A5.nnz, val_bytes=vb, x_bytes=vb, y_bytes=vb)
+            bb = model.bytes_backward(A5.n_rows, A5.n_cols, A5.nnz, val_bytes=vb, vec_bytes=vb)
+            ent = {
+                "forward_ms": ms_f, "backward_ms": ms_b, "grad_x_ms": ms_gx,
+                "backward_after_new_values_ms": ms_svb - ms_sv,
+                "forward_GBs": bf / ms_f / 1e6, "backward_GBs": bb / ms_b / 1e6,
+                "time_vs_plain": ms_b / ms_f}
+            if npdt == np.float64:
+                # grad_x: one FMA per entry; grad_val: one multiply per entry
+                ent["fp64_pipe_frac"] = fp64_frac(2 * A5.nnz, ms_b)
+            out[label] = ent
+            del v5, M5, x5, g5, y5
+        except Exception as e:
+            out[label] = {"error": repr(e)}
+    sizes = W.batch_sizes(W.BATCH_COUNT)
+    members = [W.batch_matrix(m, int(n)) for m, n in enumerate(sizes)]
+    for label, tdt in (("batched_256", torch.float64), ("batched_256_f32", torch.float32)):
+        try:  # 256 uneven matrices, one persistent launch replayed from a CUDA graph
+            npdt = np.float64 if tdt == torch.float64 else np.float32
+            vb = 8 if tdt == torch.float64 else 4
+            mats, xs, ys, b_tot, nnz_tot = [], [], [], 0, 0
+            for Am in members:
+                mats.append(Matrix.from_csr(Am.row_ptr, Am.col_idx, Am.val.astype(npdt), Am.n_cols))
+                xs.append(torch.rand(Am.n_cols, dtype=tdt, device=dev))
+                ys.append(torch.empty(Am.n_rows, dtype=tdt, device=dev))
+                b_tot += model.bytes_plain(Am.n_rows, Am.n_cols, Am.nnz, val_bytes=vb, x_bytes=vb, y_bytes=vb)
+                nnz_tot += Am.nnz
+            B = Batch(mats)
+            ms_b = _time(lambda: B.apply(xs, ys), 10)
+            ms_each = _time(lambda: [M.apply(xx, yy) for M, xx, yy in zip(mats, xs, ys)], 3)
+            out[label] = {
+                "ms": ms_b, "GBs": b_tot / ms_b / 1e6, "GFLOPs": 2 * nnz_tot / ms_b / 1e6,
+                "nnz": nnz_tot, "separate_launches_ms": ms_each,
+                "GBs_vs_plain": (b_tot / ms_b) / (b_plain / form_ms["plain"]), "plan": B.info()}
+            del B, mats, xs, ys
+        except Exception as e:
+            out[label] = {"error": repr(e)}
     return out
 
 

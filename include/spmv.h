@@ -126,14 +126,22 @@ spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
 /* Accumulator of an FP32-storage handle: 0 = one FP64 FMA per entry (operands
  * widened exactly), 1 = exact-product float-float accumulation on the FP32 pipe
- * (default; relative accuracy about 2^-44 of sum |a_ij x_j|).  FP64 handles
- * always accumulate with FP64 FMAs and ignore this setting. */
+ * (default; relative accuracy about 2^-44 of sum |a_ij x_j|).  The float-float
+ * sum splits each product exactly only inside FP32's range: a row with a nonzero
+ * product below 2^-100 in magnitude, an overflow of a product or of the running
+ * sum, or an infinite or NaN operand is summed again with FP64 FMAs (one more
+ * pass over that row's entries), so both settings give FP64-accumulation results
+ * for every input.  FP64 handles always accumulate with FP64 FMAs and ignore
+ * this setting. */
 spmv_status spmv_set_accumulator(spmv_handle h, int32_t acc);
 
 /* Plain spMVM, Listing 1 generalised: y = alpha*A*x + beta*y.
  * x: n_cols entries of type xt; y: n_rows entries of type yt.  Supported
  * (value, x, y) types: (F64, F64, F64), (F32, F32, F32), (F32, F32, F64).  FP32
- * operands are multiplied and accumulated in at least FP64-class precision.
+ * operands: every product of two floats is exact, and the row sums carry at
+ * least 44 significant bits (float-float, see spmv_set_accumulator) over FP64's
+ * exponent range (rows outside FP32's go through FP64 FMAs), within
+ * 1e-6 * sum_j |a_ij x_j| of the FP64 sum; an FP32 y is then rounded once.
  * x and y must not overlap. */
 spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt,
                        double beta, void *y, spmv_dtype yt, void *stream);
@@ -234,23 +242,26 @@ spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_i
 /* Transposed CRS build that allocates nothing (no counterpart in the paper).
  *
  * Some callers cannot allocate device memory at the moment they need this
- * result: code running while a CUDA graph is being captured (cudaMalloc is not
- * a capturable operation), real-time or latency-bound loops that must not wait
- * on the allocator or risk an out-of-memory failure mid-run, and programs whose
- * device memory is already reserved by another allocator.  This entry point
- * builds the same structure as spmv_get_transpose from CRS arrays already on
- * the device and writes it to caller-provided device buffers; its scratch (one
- * counter per column plus the scan's block sums) is a fixed array compiled into
+ * result: real-time or latency-bound loops that must not wait on the allocator
+ * or risk an out-of-memory failure mid-run, and programs whose device memory is
+ * already reserved by another allocator (a pool that owns the whole device).
+ * This entry point builds the same structure as spmv_get_transpose from CRS
+ * arrays already on the device and writes it to caller-provided device
+ * buffers; its scratch (one counter per column, the scans' block sums and the
+ * histograms of the column sort, about 6.3 MB) is a fixed array compiled into
  * the library, which every GPU that loads the library holds until the process
- * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ * work is linear in nnz whatever the column lengths (a stable radix sort of
+ * the entries by column).
  *
  *   row_ptr[n_rows+1], col_idx[nnz]: a valid CRS structure on the device;
  *   rowT_ptr[n_cols+1], colT_idx[nnz], perm[nnz]: device outputs, as for
  *   spmv_get_transpose (rows of A^T in increasing position of A).
  * n_cols must not exceed SPMV_NOALLOC_MAX_COLS (larger sizes return
- * SPMV_ERR_UNSUPPORTED before any work is enqueued).  Entries outside the CRS
- * rules are skipped rather than followed, so the output is then not a
- * transpose, but no memory outside the arrays is touched.
+ * SPMV_ERR_UNSUPPORTED before any work is enqueued).  The arrays are not
+ * validated: a column outside [0, n_cols) is left out of rowT_ptr (and placed
+ * after the last row of A^T), so the output is then not a transpose, but no
+ * memory outside the arrays is touched.
  * The first call on a device looks up the scratch array's device address (once
  * per device, with that device current); make that first call before any
  * stream capture.  Every call shares the one array and re-clears the part it
@@ -269,7 +280,8 @@ spmv_status spmv_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
 /* Group count matrix handles (all FP64 or all FP32 storage) into one batch whose
  * apply is a single persistent kernel launch over the warp chunks of every
  * matrix (the slot-major chunk kernel on one concatenated slot-major copy of all
- * matrices, 7 entries per lane), captured once into a CUDA graph and replayed.
+ * matrices), captured once into a CUDA graph and replayed.  spmv_batched_get_info
+ * reports the entries per lane the batch runs with.
  * The batch holds its own copy of the values: after spmv_set_values on a member,
  * the next spmv_batched_apply lays that member's values out again (on stream,
  * before the launch).  The handles must outlive the batch. */

@@ -109,7 +109,20 @@ __global__ void __launch_bounds__(kDotThreads) k_dot_f32v(const float4 *__restri
         c3.fma(u.w, v.w);
     }
     if (blockIdx.x == 0 && threadIdx.x < tail) c0.fma(at[threadIdx.x], bt[threadIdx.x]);
-    finish(block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red), o, s_red);
+    double t = (c0.get() + c1.get()) + (c2.get() + c3.get());
+    if (c0.poisoned() || c1.poisoned() || c2.poisoned() || c3.poisoned()) {
+        // a product outside FP32's range: this thread's terms again with exact FP64 products
+        t = 0.0;
+        for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 u = __ldg(a + i), v = __ldg(b + i);
+            t = fma(widen(u.x), widen(v.x), t);
+            t = fma(widen(u.y), widen(v.y), t);
+            t = fma(widen(u.z), widen(v.z), t);
+            t = fma(widen(u.w), widen(v.w), t);
+        }
+        if (blockIdx.x == 0 && threadIdx.x < tail) t = fma(widen(at[threadIdx.x]), widen(bt[threadIdx.x]), t);
+    }
+    finish(block_sum(t, s_red), o, s_red);
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_dot_f64v(const double2 *__restrict__ a,
@@ -186,7 +199,20 @@ __global__ void __launch_bounds__(kDotThreads) k_update32v(float4 *__restrict__ 
         rt[j] = ri;
         c0.fma(ri, ri);
     }
-    finish(block_sum((c0.get() + c1.get()) + (c2.get() + c3.get()), s_red), o, s_red);
+    double t = (c0.get() + c1.get()) + (c2.get() + c3.get());
+    if (c0.poisoned() || c1.poisoned() || c2.poisoned() || c3.poisoned()) {
+        // a square outside FP32's range: this thread's updated r again in FP64
+        t = 0.0;
+        for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 rv = r[i];
+            t = fma(widen(rv.x), widen(rv.x), t);
+            t = fma(widen(rv.y), widen(rv.y), t);
+            t = fma(widen(rv.z), widen(rv.z), t);
+            t = fma(widen(rv.w), widen(rv.w), t);
+        }
+        if (blockIdx.x == 0 && threadIdx.x < tail) t = fma(widen(rt[threadIdx.x]), widen(rt[threadIdx.x]), t);
+    }
+    finish(block_sum(t, s_red), o, s_red);
 }
 
 __global__ void __launch_bounds__(kDotThreads) k_direction32v(float4 *__restrict__ p,

@@ -145,6 +145,21 @@ struct AccF64 {
 // addition plus pl is collected in l.  The value is h + l; its error is about
 // n^2 2^-48 sum |a_ij x_j| for n terms, far inside the FP32-storage tolerance,
 // while using no FP64 instructions per entry.
+//
+// The scheme needs every product inside FP32's range.  Outside it the sum is
+// marked untrustworthy ("poisoned": l is NaN) and the caller sums the row again
+// with exact FP64 products (FP64 accumulation, the definition of this form):
+//   * a nonzero product of magnitude below kFFTiny may have lost bits of its
+//     exact split to FP32 underflow (the low part's last bit lies 47 binades
+//     below the high part's leading one, and FP32 stops at 2^-149), or have
+//     underflowed to zero altogether: fma() sets l to NaN for it;
+//   * an overflow of a product or of the running sum makes the two-sum form
+//     inf - inf, so l becomes NaN by itself, as it does for an infinite or NaN
+//     operand.
+// A poisoned row costs one FP64 pass over its entries; rows of ordinary
+// magnitudes never take it.
+constexpr float kFFTiny = 0x1p-100f;
+
 struct AccFF {
     float h, l;
     __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }
@@ -158,11 +173,41 @@ struct AccFF {
     __device__ __forceinline__ void fma(float v, float x) {
         const float ph = v * x;
         const float pl = fmaf(v, x, -ph);
-        add_pair(ph, pl);
+        const bool tiny = fabsf(ph) < kFFTiny && v != 0.0f && x != 0.0f;
+        add_pair(ph, tiny ? __int_as_float(0x7fffffff) : pl);
     }
     __device__ __forceinline__ void add(const AccFF &o) { add_pair(o.h, o.l); }
+    __device__ __forceinline__ bool poisoned() const { return l != l; }
     __device__ __forceinline__ double get() const { return widen(h) + widen(l); }
 };
+
+// Row r of m summed again with exact FP64 products of its (FP32-stored)
+// operands, in CRS order: the fallback for a poisoned float-float row sum (see
+// AccFF).  x[j] is read at x + j*ldx.
+template <typename VT, bool INDIRECT, typename XT>
+__device__ __forceinline__ double row_sum_exact(const MatRef m, int64_t r, const XT *__restrict__ x, int64_t ldx = 1) {
+    double s = 0.0;
+    const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
+    for (int k = kb; k < ke; ++k) {
+        VT v;
+        if constexpr (INDIRECT)
+            v = __ldg(static_cast<const VT *>(m.vind) + __ldg(static_cast<const int32_t *>(m.vs) + k));
+        else
+            v = __ldg(static_cast<const VT *>(m.vs) + k);
+        s = fma(widen(v), widen(__ldg(x + static_cast<int64_t>(__ldg(m.col + k)) * ldx)), s);
+    }
+    return s;
+}
+
+// The row sum of a finished accumulator: a poisoned float-float sum is summed
+// again from the CRS arrays of m (row r, operand x); anything else as it is.
+template <typename VT, bool INDIRECT, typename XT, typename ACC>
+__device__ __forceinline__ double acc_value(const ACC &a, const MatRef &m, int64_t r, const XT *__restrict__ x) {
+    if constexpr (std::is_same<ACC, AccFF>::value) {
+        if (a.poisoned()) return row_sum_exact<VT, INDIRECT>(m, r, x);
+    }
+    return a.get();
+}
 
 template <typename V, typename X> __device__ __forceinline__ X ldg_x(const X *p) { return __ldg(p); }
 

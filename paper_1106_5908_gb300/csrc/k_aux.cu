@@ -2,6 +2,7 @@
 // reduction), the halo gather of the split form, the per-entry gradient of the
 // reverse pass, the on-device transposed-CRS build and value conversions.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 #include "common.cuh"
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(256) k_rowvec(const KParams p, int32_t n_rows)
 #pragma unroll
     for (int o = T / 2; o >= 1; o >>= 1) acc.add(shfl_xor_acc(acc, o, mask));
     if (lane == 0) {
-        const double v = acc.get();
+        const double v = acc_value<VT, false>(acc, p.m, row, x);
         double out;
         if (p.alpha == 1.0 && p.beta == 0.0) out = v;
         else if (p.beta == 0.0) out = p.alpha * v;
@@ -414,89 +415,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int32_t *__re
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offs[blockIdx.x] + tot;
 }
 
-__global__ void k_fill_transpose(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                 int32_t n_rows, int32_t *cursor, int32_t *colT, int32_t *perm) {
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_rows;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int kb = rp[i], ke = rp[i + 1];
-        for (int k = kb; k < ke; ++k) {
-            const int pos = atomicAdd(cursor + col[k], 1);
-            colT[pos] = static_cast<int32_t>(i);
-            perm[pos] = k;
-        }
-    }
-}
-
-// Insertion sort of each row of A^T by original position (rows of A^T are short
-// for the stencil and Hamiltonian-like patterns; cost is quadratic in row length).
-__global__ void k_sort_rowsT(const int32_t *__restrict__ rowT, int32_t n_cols, int32_t *colT,
-                             int32_t *perm) {
-    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n_cols;
-         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int b = rowT[j], e = rowT[j + 1];
-        for (int u = b + 1; u < e; ++u) {
-            const int32_t pk = perm[u], ck = colT[u];
-            int v = u - 1;
-            while (v >= b && perm[v] > pk) {
-                perm[v + 1] = perm[v];
-                colT[v + 1] = colT[v];
-                --v;
-            }
-            perm[v + 1] = pk;
-            colT[v + 1] = ck;
-        }
-    }
-}
-
-cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp,
-                             const int32_t *col, int32_t *rowT, int32_t *colT, int32_t *perm,
-                             int32_t *work, cudaStream_t s) {
-    // work: n_cols + 1 counts/cursors followed by the scan block sums
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (static_cast<size_t>(n_cols) + 1), s);
-    if (e != cudaSuccess) return e;
-    if (nnz > 0) {
-        k_count_cols<<<8 * sms, 256, 0, s>>>(col, nnz, work);
-    }
-    const int64_t nb = (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk;
-    int32_t *sums = work + n_cols + 1;
-    if (n_cols > 0) {
-        k_scan_partial<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums);
-        k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, static_cast<int32_t>(nb));
-        k_scan_final<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums, rowT);
-    } else {
-        e = cudaMemsetAsync(rowT, 0, sizeof(int32_t), s);
-        if (e != cudaSuccess) return e;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (nnz > 0) {
-        e = cudaMemcpyAsync(work, rowT, sizeof(int32_t) * static_cast<size_t>(n_cols),
-                            cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return e;
-        k_fill_transpose<<<4 * sms, 256, 0, s>>>(rp, col, n_rows, work, colT, perm);
-        k_sort_rowsT<<<4 * sms, 256, 0, s>>>(rowT, n_cols, colT, perm);
-    }
-    return cudaGetLastError();
-}
-
-// Work-array length (int32 entries) launch_transpose needs.
-int64_t transpose_work_len(int32_t n_cols) {
-    return static_cast<int64_t>(n_cols) + 1 + (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk + 1;
-}
-
-// ---------------------------------------------------------------------------
-// Transposed build without allocation.  Its work array (column counts, then
-// cursors, then the scan's block sums) lives in one fixed device array that
-// every GPU loading the library holds until the process exits.  Entries whose
-// column or row range is outside the stated sizes are skipped, so a malformed
-// input cannot make these kernels touch memory outside their arrays.
-// ---------------------------------------------------------------------------
-constexpr int64_t kNoAllocMaxCols = 1 << 20;
-constexpr int64_t kNoAllocWorkLen = kNoAllocMaxCols + 1 + (kNoAllocMaxCols + kScanChunk - 1) / kScanChunk + 1;
-static __device__ __align__(256) int32_t g_transpose_scratch[kNoAllocWorkLen];
-
+// Counts of the columns inside [0, n_cols) only (inputs that were not validated).
 __global__ void k_count_cols_checked(const int32_t *__restrict__ col, int64_t nnz, int32_t n_cols,
                                      int32_t *cnt) {
     for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nnz;
@@ -506,31 +425,229 @@ __global__ void k_count_cols_checked(const int32_t *__restrict__ col, int64_t nn
     }
 }
 
-__global__ void k_fill_transpose_checked(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                         int32_t n_rows, int32_t n_cols, int64_t nnz, int32_t *cursor,
-                                         int32_t *colT, int32_t *perm) {
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_rows;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t kb = max(static_cast<int64_t>(rp[i]), static_cast<int64_t>(0));
-        const int64_t ke = min(static_cast<int64_t>(rp[i + 1]), nnz);
-        for (int64_t k = kb; k < ke; ++k) {
-            const int32_t c = col[k];
-            if (c < 0 || c >= n_cols) continue;
-            const int pos = atomicAdd(cursor + c, 1);
-            if (pos >= 0 && pos < nnz) {
-                colT[pos] = static_cast<int32_t>(i);
-                perm[pos] = static_cast<int32_t>(k);
-            }
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of the entry indices k = 0..nnz-1 by column (8-bit
+// digits, as many passes as the column range needs).  The entries of each
+// column of A end up in increasing k, so every row of A^T lists its entries by
+// increasing row of A: the unique order the oracle defines.  A pass is a digit
+// histogram per CTA range, one exclusive scan of the histograms (digit-major,
+// so the ranges of a digit follow each other in CTA order), and a stable
+// scatter in which each CTA walks its range in order, 256 entries per round;
+// inside a round a warp's entries find their equal-digit peers with a match
+// instruction, and the warps' counts are combined in warp order.  The work is
+// O(passes * nnz) whatever the column lengths (one dense column costs what a
+// stencil costs), and the result does not depend on any atomic order.  The
+// key of entry k is read as col[k] in every pass, so only the entry indices
+// move (ping-pong between the two output arrays).  A column outside
+// [0, n_cols) gets key n_cols (it sorts last; only the allocation-free entry
+// point can meet one).
+// ---------------------------------------------------------------------------
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kRadixThreads = 256;  // one digit per thread
+constexpr int kRadixMaxGrid = 1024;
+constexpr int64_t kRadixHistLen = static_cast<int64_t>(kRadixBins) * kRadixMaxGrid;
+static_assert(kRadixThreads == kRadixBins, "the scatter gives each thread one digit");
+
+__device__ __forceinline__ int32_t radix_key(const int32_t *__restrict__ col, int32_t k, int32_t n_cols) {
+    const int32_t c = __ldg(col + k);
+    return (c >= 0 && c < n_cols) ? c : n_cols;
+}
+
+// hist[d * grid + g] = entries of CTA range g whose key has digit d.  vin: entry
+// indices of the previous pass (nullptr: k itself).
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const int32_t *__restrict__ col,
+                                                              const int32_t *__restrict__ vin, int64_t nnz,
+                                                              int32_t n_cols, int shift, int64_t per,
+                                                              int32_t *__restrict__ hist) {
+    __shared__ int32_t s_cnt[kRadixBins];
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * per;
+    const int64_t e = min(nnz, b + per);
+    for (int64_t i = b + threadIdx.x; i < e; i += kRadixThreads) {
+        const int32_t k = vin ? vin[i] : static_cast<int32_t>(i);
+        atomicAdd(&s_cnt[(radix_key(col, k, n_cols) >> shift) & (kRadixBins - 1)], 1);
+    }
+    __syncthreads();
+    hist[static_cast<int64_t>(threadIdx.x) * gridDim.x + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Stable scatter of CTA range g: offs holds the exclusive scan of hist.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const int32_t *__restrict__ col,
+                                                                 const int32_t *__restrict__ vin, int64_t nnz,
+                                                                 int32_t n_cols, int shift, int64_t per,
+                                                                 const int32_t *__restrict__ offs,
+                                                                 int32_t *__restrict__ vout) {
+    constexpr int NW = kRadixThreads / 32;
+    __shared__ int32_t s_base[kRadixBins];   // next output position of each digit for this CTA
+    __shared__ int32_t s_wc[NW][kRadixBins]; // a round's per-warp digit counts, then offsets
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    s_base[t] = offs[static_cast<int64_t>(t) * gridDim.x + blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) s_wc[q][t] = 0;
+    __syncthreads();
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * per;
+    const int64_t e = min(nnz, b + per);
+    for (int64_t r0 = b; r0 < e; r0 += kRadixThreads) {
+        const int64_t i = r0 + t;
+        const bool ok = i < e;
+        int32_t k = 0;
+        int d = kRadixBins;  // past the range: its own peer group, never written
+        if (ok) {
+            k = vin ? vin[i] : static_cast<int32_t>(i);
+            d = (radix_key(col, k, n_cols) >> shift) & (kRadixBins - 1);
         }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) s_wc[w][d] = __popc(peers);
+        __syncthreads();
+        int32_t run = s_base[t];  // digit t: warps in order
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+            const int32_t c = s_wc[q][t];
+            s_wc[q][t] = run;
+            run += c;
+        }
+        s_base[t] = run;
+        __syncthreads();
+        if (ok) {
+            const int64_t pos = static_cast<int64_t>(s_wc[w][d]) + rank;
+            if (pos >= 0 && pos < nnz) vout[pos] = k;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NW; ++q) s_wc[q][t] = 0;
+        __syncthreads();
     }
 }
+
+__global__ void k_iota(int32_t *__restrict__ out, int64_t n) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = static_cast<int32_t>(i);
+}
+
+// colT[p] = the row of A holding entry perm[p]: the last row i with
+// rp[i] <= perm[p] (binary search over rp[0..n_rows - 1], every read inside it).
+__global__ void k_rows_of_entries(const int32_t *__restrict__ rp, int32_t n_rows, const int32_t *__restrict__ perm,
+                                  int64_t nnz, int32_t *__restrict__ colT) {
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < nnz;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t k = perm[p];
+        int32_t lo = 0, hi = n_rows - 1;
+        while (lo < hi) {
+            const int32_t mid = lo + (hi - lo + 1) / 2;
+            if (__ldg(rp + mid) <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        colT[p] = lo;
+    }
+}
+
+static int radix_passes(int32_t n_cols) {
+    // keys lie in [0, n_cols] (n_cols: an invalid column)
+    int bits = 0;
+    while (bits < 31 && (static_cast<int64_t>(n_cols) >> bits) != 0) ++bits;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+// Exclusive scan of n int32 counts into out[0..n] (out[n] = total); sums holds
+// (n + kScanChunk - 1) / kScanChunk + 1 entries.
+static cudaError_t scan_counts(const int32_t *in, int64_t n, int32_t *sums, int32_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    k_scan_partial<<<static_cast<int>(nb), kScanThreads, 0, s>>>(in, n, sums);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, static_cast<int32_t>(nb));
+    k_scan_final<<<static_cast<int>(nb), kScanThreads, 0, s>>>(in, n, sums, out);
+    return cudaGetLastError();
+}
+
+// Work layout of the transposed build (int32 entries): column counts
+// (n_cols + 1), the column scan's block sums, the radix histograms, their scan
+// (kRadixHistLen + 1) and its block sums.
+static int64_t col_sums_len(int32_t n_cols) { return (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk + 1; }
+constexpr int64_t kHistSumsLen = (kRadixHistLen + kScanChunk - 1) / kScanChunk + 1;
+
+int64_t transpose_work_len(int32_t n_cols) {
+    return static_cast<int64_t>(n_cols) + 1 + col_sums_len(n_cols) + 2 * kRadixHistLen + 1 + kHistSumsLen;
+}
+
+// The transposed structure into rowT (n_cols + 1), colT and perm (nnz each),
+// with `work` of transpose_work_len(n_cols) entries.  checked: the arrays were
+// not validated, so columns outside [0, n_cols) are left out of the counts (and
+// sort last) and every read and write stays inside the stated sizes.
+static cudaError_t transpose_into(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp, const int32_t *col,
+                                  int32_t *rowT, int32_t *colT, int32_t *perm, int32_t *work, bool checked,
+                                  cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int32_t *cnt = work;
+    int32_t *cnt_sums = cnt + n_cols + 1;
+    int32_t *hist = cnt_sums + col_sums_len(n_cols);
+    int32_t *offs = hist + kRadixHistLen;
+    int32_t *hist_sums = offs + kRadixHistLen + 1;
+    // row pointer of A^T: counts per column, exclusive scan
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (static_cast<size_t>(n_cols) + 1), s);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0) {
+        if (checked) k_count_cols_checked<<<8 * sms, 256, 0, s>>>(col, nnz, n_cols, cnt);
+        else k_count_cols<<<8 * sms, 256, 0, s>>>(col, nnz, cnt);
+    }
+    if ((e = scan_counts(cnt, n_cols, cnt_sums, rowT, s)) != cudaSuccess) return e;
+    if (nnz <= 0) return cudaGetLastError();
+    // entry order: stable sort of k by column; the last pass writes perm
+    const int passes = radix_passes(n_cols);
+    if (passes == 0) {
+        k_iota<<<4 * sms, 256, 0, s>>>(perm, nnz);
+    } else {
+        int64_t grid = (nnz + 4095) / 4096;
+        if (grid > kRadixMaxGrid) grid = kRadixMaxGrid;
+        const int64_t per = (nnz + grid - 1) / grid;
+        const int32_t *src = nullptr;
+        for (int j = 0; j < passes; ++j) {
+            int32_t *dst = ((passes - 1 - j) % 2 == 0) ? perm : colT;
+            const int shift = j * kRadixBits;
+            k_radix_hist<<<static_cast<int>(grid), kRadixThreads, 0, s>>>(col, src, nnz, n_cols, shift, per, hist);
+            if ((e = scan_counts(hist, kRadixBins * grid, hist_sums, offs, s)) != cudaSuccess) return e;
+            k_radix_scatter<<<static_cast<int>(grid), kRadixThreads, 0, s>>>(col, src, nnz, n_cols, shift, per, offs,
+                                                                            dst);
+            src = dst;
+        }
+    }
+    if (n_rows > 0) k_rows_of_entries<<<8 * sms, 256, 0, s>>>(rp, n_rows, perm, nnz, colT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *rp, const int32_t *col,
+                             int32_t *rowT, int32_t *colT, int32_t *perm, int32_t *work, cudaStream_t s) {
+    return transpose_into(n_rows, n_cols, nnz, rp, col, rowT, colT, perm, work, false, s);
+}
+
+// ---------------------------------------------------------------------------
+// Transposed build without allocation.  Its work array (column counts, the
+// column scan's block sums, the radix histograms and their scan) lives in one
+// fixed device array that every GPU loading the library holds until the
+// process exits.  The inputs are not validated: columns outside [0, n_cols) are
+// left out and every read and write stays inside the stated sizes.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxCols = 1 << 20;
+constexpr int64_t kNoAllocWorkLen = kNoAllocMaxCols + 1 + (kNoAllocMaxCols + kScanChunk - 1) / kScanChunk + 1 +
+                                   2 * kRadixHistLen + 1 + kHistSumsLen;
+static __device__ __align__(256) int32_t g_transpose_scratch[kNoAllocWorkLen];
 
 int64_t transpose_noalloc_max_cols() { return kNoAllocMaxCols; }
 
 // Device address of the fixed work array on the current device, looked up once
-// per device (host code cannot use the array's name as a device address).
+// per device with that device current (host code cannot use the array's name as
+// a device address).  The lookup is serialised, so host threads making their
+// first calls at the same time get the same address.  A cudaDeviceReset unloads
+// the module and the cached address with it: the library does not support
+// calls after one.
 static int32_t *noalloc_scratch_ptr(cudaError_t *err) {
     constexpr int kMaxDevices = 64;
+    static std::mutex mu;
     static int32_t *ptrs[kMaxDevices] = {nullptr};
     int dev = 0;
     *err = cudaGetDevice(&dev);
@@ -539,6 +656,7 @@ static int32_t *noalloc_scratch_ptr(cudaError_t *err) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
+    std::lock_guard<std::mutex> lock(mu);
     if (ptrs[dev] == nullptr) {
         void *p = nullptr;
         *err = cudaGetSymbolAddress(&p, g_transpose_scratch);
@@ -555,32 +673,9 @@ cudaError_t launch_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz
     cudaError_t e = cudaSuccess;
     int32_t *work = noalloc_scratch_ptr(&e);
     if (!work) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // the array keeps the previous call's contents: clear the counts first
-    e = cudaMemsetAsync(work, 0, sizeof(int32_t) * (static_cast<size_t>(n_cols) + 1), s);
-    if (e != cudaSuccess) return e;
-    if (nnz > 0) k_count_cols_checked<<<8 * sms, 256, 0, s>>>(col, nnz, n_cols, work);
-    const int64_t nb = (static_cast<int64_t>(n_cols) + kScanChunk - 1) / kScanChunk;
-    int32_t *sums = work + n_cols + 1;
-    if (n_cols > 0) {
-        k_scan_partial<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums);
-        k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, static_cast<int32_t>(nb));
-        k_scan_final<<<static_cast<int>(nb), kScanThreads, 0, s>>>(work, n_cols, sums, rowT);
-    } else {
-        e = cudaMemsetAsync(rowT, 0, sizeof(int32_t), s);
-        if (e != cudaSuccess) return e;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (nnz > 0) {
-        e = cudaMemcpyAsync(work, rowT, sizeof(int32_t) * static_cast<size_t>(n_cols),
-                            cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return e;
-        k_fill_transpose_checked<<<4 * sms, 256, 0, s>>>(rp, col, n_rows, n_cols, nnz, work, colT, perm);
-        k_sort_rowsT<<<4 * sms, 256, 0, s>>>(rowT, n_cols, colT, perm);
-    }
-    return cudaGetLastError();
+    // the array keeps the previous call's contents; transpose_into clears what
+    // must start at zero (the column counts) and overwrites the rest
+    return transpose_into(n_rows, n_cols, nnz, rp, col, rowT, colT, perm, work, true, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_pipe(const WarpParams p) {
             chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
             for (int q = lane; q < r1 - r0; q += 32)
-                store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
+                store_acc<VT, INDIRECT>(m, x, y, r0 + q, srow[q], alpha, beta, plain);
         }
         // every lane is done with stage s (and the row buffer) before lane 0
         // refills it at the next iteration
@@ -369,7 +369,7 @@ k_pipe3(const WarpParams p) {
             const bool ends = (base + off + E >= d.k1) || (lane < 31 && (next_bits & 1u));
             chunk_lane<E, VT, XT, ACC>(vals, xcur, mbits, lo, hi, ends, r0, srow, lane);
             __syncwarp();
-            for (int q = lane; q < r1 - r0; q += 32) store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
+            for (int q = lane; q < r1 - r0; q += 32) store_acc<VT, INDIRECT>(m, x, y, r0 + q, srow[q], alpha, beta, plain);
         }
         __syncwarp();  // stage s and the row buffer are free again
 #pragma unroll

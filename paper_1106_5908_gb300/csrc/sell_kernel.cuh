@@ -77,18 +77,19 @@ __device__ __forceinline__ void sell_fma_tail(ACC (&acc)[kSellK], const VT (&v)[
     }
 }
 
-// Final store of a row; `old` is y[row] widened, loaded ahead (read only when
-// beta is nonzero).
-template <typename YT, typename ACC>
-__device__ __forceinline__ void sell_store(YT *__restrict__ y, int row, const ACC &a, double alpha, double beta,
-                                           bool plain, double old) {
+// Final store of stored row `row` of m; `old` is y[row] widened, loaded ahead
+// (read only when beta is nonzero).  A poisoned float-float sum is summed again
+// in FP64 from the CRS arrays of m.
+template <typename VT, typename XT, typename YT, typename ACC>
+__device__ __forceinline__ void sell_store(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y, int row,
+                                           const ACC &a, double alpha, double beta, bool plain, double old) {
     if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
-        if (plain) {
+        if (plain && !a.poisoned()) {
             y[row] = a.h + a.l;
             return;
         }
     }
-    const double v = a.get();
+    const double v = acc_value<VT, false>(a, m, row, x);
     double out;
     if (plain) out = v;
     else if (beta == 0.0) out = alpha * v;
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
             if (last_of(ca)) {
 #pragma unroll
                 for (int h = 0; h < K; ++h) {
-                    if (P.r[h] >= 0) sell_store(y, P.r[h], acc[h], alpha, beta, plain, P.y[h]);
+                    if (P.r[h] >= 0) sell_store<VT>(p.m, x, y, P.r[h], acc[h], alpha, beta, plain, P.y[h]);
                     acc[h].zero();
                 }
             }

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
                 epi.store(y, srow, r1 - r0, alpha, beta, emode, lane);
             } else {
                 for (int q = lane; q < r1 - r0; q += 32)
-                    store_acc(y, r0 + q, srow[q], alpha, beta, plain, m.rmap);
+                    store_acc<VT, false>(m, x, y, r0 + q, srow[q], alpha, beta, plain);
             }
         }
         __syncwarp();  // the row buffer is free again

@@ -246,8 +246,12 @@ __global__ void __launch_bounds__(NT) k_tile(const KParams p) {
             for (int idx = tid; idx < nrows * R; idx += NT) {
                 const int i_r = idx / R;
                 const int rr = idx % R;
-                const double v = s_y[idx];
+                double v = s_y[idx];
                 s_y[idx] = 0.0;
+                if constexpr (std::is_same<ACC, AccFF>::value) {
+                    // a poisoned float-float sum arrives as NaN: sum the row again in FP64
+                    if (v != v && rr < p.rhs_count) v = row_sum_exact<VT, INDIRECT>(m, r0 + i_r, x + rr, p.ldx);
+                }
                 if (rr < p.rhs_count) {
                     YT *yp = y + static_cast<int64_t>(r0 + i_r) * p.ldy + rr;
                     double out;
@@ -280,7 +284,10 @@ __global__ void __launch_bounds__(NT) k_tile(const KParams p) {
             if (g == 0 && lane_ok) {
                 ACC tot = s_carry[r];
                 for (int u = 1; u < G; ++u) tot.add(s_carry[u * R + r]);
-                const double v = tot.get();
+                double v = tot.get();
+                if constexpr (std::is_same<ACC, AccFF>::value) {
+                    if (tot.poisoned()) v = row_sum_exact<VT, INDIRECT>(m, r0, x + r, p.ldx);
+                }
                 YT *yp = y + static_cast<int64_t>(r0) * p.ldy + r;
                 double out;
                 if (plain_store) out = v;

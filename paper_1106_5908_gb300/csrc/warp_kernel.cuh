@@ -84,20 +84,26 @@ __device__ __forceinline__ void store_row(YT *__restrict__ y, int64_t row, doubl
     y[row] = narrow<YT>(out);
 }
 
-// Store a finished row sum.  A float-float sum bound for an FP32 y with
-// alpha = 1, beta = 0 is rounded to float directly (h + l on the FP32 pipe);
-// every other case goes through FP64.
-template <typename YT, typename ACC>
-__device__ __forceinline__ void store_acc(YT *__restrict__ y, int64_t row, const ACC &a, double alpha,
-                                          double beta, bool plain, const int32_t *rmap) {
-    if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
-        if (plain) {
-            if (rmap) row = __ldg(rmap + row);
-            y[row] = a.h + a.l;
+// Store the finished row sum of stored row `row` of m (output row through
+// m.rmap).  A float-float sum bound for an FP32 y with alpha = 1, beta = 0 is
+// rounded to float directly (h + l on the FP32 pipe); a poisoned one is summed
+// again in FP64; every other case goes through FP64.
+template <typename VT, bool INDIRECT, typename XT, typename YT, typename ACC>
+__device__ __forceinline__ void store_acc(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y,
+                                          int64_t row, const ACC &a, double alpha, double beta, bool plain) {
+    if constexpr (std::is_same<ACC, AccFF>::value) {
+        if (a.poisoned()) {
+            store_row(y, row, row_sum_exact<VT, INDIRECT>(m, row, x), alpha, beta, plain, m.rmap);
             return;
         }
+        if constexpr (std::is_same<YT, float>::value) {
+            if (plain) {
+                y[m.rmap ? __ldg(m.rmap + row) : row] = a.h + a.l;
+                return;
+            }
+        }
     }
-    store_row(y, row, a.get(), alpha, beta, plain, rmap);
+    store_row(y, row, a.get(), alpha, beta, plain, m.rmap);
 }
 
 // Form of the update y = alpha*v + beta*y, decided once per launch so that no
@@ -137,18 +143,12 @@ struct RowEpilogue {
     template <typename ACC>
     __device__ __forceinline__ void store(YT *__restrict__ y, const ACC *srow, int nrows, double alpha,
                                           double beta, int mode, int lane) const {
+        static_assert(std::is_same<ACC, AccF64>::value, "row-mapped products accumulate in FP64");
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int q = lane + 32 * k;
             if (q >= nrows) break;
-            const ACC a = srow[q];
-            if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
-                if (mode == kEpiPlain) {
-                    y[dst[k]] = a.h + a.l;
-                    continue;
-                }
-            }
-            const double v = a.get();
+            const double v = srow[q].get();
             double out;
             if (mode == kEpiPlain) out = v;
             else if (mode == kEpiScale) out = alpha * v;
@@ -198,7 +198,7 @@ __device__ __forceinline__ void long_row(const MatRef &m, const ChunkDesc &d, co
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) acc.add(shfl_xor_acc2(acc, o));
-    if (lane == 0) store_acc(y, d.r0, acc, alpha, beta, plain, m.rmap);
+    if (lane == 0) store_acc<VT, INDIRECT>(m, x, y, d.r0, acc, alpha, beta, plain);
 }
 
 // A chunk with empty rows: one row per lane straight from global memory.
@@ -217,7 +217,7 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
             else
                 acc.fma(__ldg(static_cast<const VT *>(m.vs) + k), xv);
         }
-        store_acc(y, r, acc, alpha, beta, plain, m.rmap);
+        store_acc<VT, INDIRECT>(m, x, y, r, acc, alpha, beta, plain);
     }
 }
 
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256) k_warp(const WarpParams p) {
     ACC *srow = s_rows[wib];
     chunk_lane<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, r0, srow, lane);
     __syncwarp();
-    for (int i = lane; i < r1 - r0; i += 32) store_acc(y, r0 + i, srow[i], alpha, beta, plain, m.rmap);
+    for (int i = lane; i < r1 - r0; i += 32) store_acc<VT, INDIRECT>(m, x, y, r0 + i, srow[i], alpha, beta, plain);
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>

@@ -96,15 +96,16 @@ def bytes_spmm(n_rows: int, n_cols: int, nnz: int, nrhs: int,
 
 
 def bytes_backward(n_rows: int, n_cols: int, nnz: int, grad_x: bool = True,
-                   grad_val: bool = True) -> int:
+                   grad_val: bool = True, val_bytes: int = 8, vec_bytes: int = 8) -> int:
     """grad_x through the transposed CRS (colT + perm per entry, val read through
     perm, rowT_ptr, g read once, grad_x written once) and grad_val (col_idx read,
-    row_ptr, x and g read once, grad_val written)."""
+    row_ptr, x and g read once, grad_val written); val_bytes / vec_bytes 4 for
+    FP32 storage."""
     b = 0
     if grad_x:
-        b += (4 + 4 + 8) * nnz + 4 * (n_cols + 1) + 8 * n_rows + 8 * n_cols
+        b += (4 + 4 + val_bytes) * nnz + 4 * (n_cols + 1) + vec_bytes * (n_rows + n_cols)
     if grad_val:
-        b += (4 + 8) * nnz + 4 * (n_rows + 1) + 8 * n_cols + 8 * n_rows
+        b += (4 + val_bytes) * nnz + 4 * (n_rows + 1) + vec_bytes * (n_cols + n_rows)
     return int(b)
 
 

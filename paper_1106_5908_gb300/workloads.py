@@ -31,6 +31,7 @@ SEED_BATCH = 4402
 SEED_STENCIL27_VAL = 5501
 SEED_STENCIL27_X = 5502
 SEED_STENCIL27_G = 5503
+SEED_FP32_RANGE = 7701
 
 
 @dataclass
@@ -303,3 +304,93 @@ BLOCK_NRHS = (1, 4, 8, 16, 32)
 BATCH_COUNT = 256
 STENCIL27_GRID = 128          # 3D 27-point, N = 2,097,152
 STENCIL27_FD_GRID = 16
+
+
+def fp32_range_case(seed: int = SEED_FP32_RANGE, n_normal: int = 3000, n_wild: int = 400,
+                    long_len: int = 3000, special: bool = True):
+    """FP32-stored values and vector whose products leave FP32's range, mixed
+    into ordinary rows (for the FP32-storage parity tests).  Returns (CRS with
+    float32 values, x float32).
+
+    x holds special values at fixed positions (1e20, -1e20, 1e-25, -1e-25, 1,
+    1.8e19, 2^-50, 2^-51, a subnormal, 0, 3e38, 1.5, and with ``special`` inf and
+    NaN); designed rows reach products above FLT_MAX (alone, cancelling, and as a
+    sum of two products below it), products far below the smallest subnormal
+    (alone, cancelling, next to a product of one), products on either side of
+    2^-100, zero values and zero x, and inf/NaN operands; ``n_wild`` rows draw
+    values and x entries with log-uniform magnitudes over the whole FP32 range
+    and ``n_wild/2`` rows over [2^-149, 2^-50] only (every product below 2^-100);
+    one row has ``long_len`` entries of the first kind; ``n_normal`` rows are N(0,1) values on
+    U[-1,1] entries.  The rows are shuffled, so chunks and slices mix them."""
+    rng = np.random.default_rng(seed)
+    spec = [1e20, -1e20, 1e-25, -1e-25, 1.0, 1.8e19, 2.0 ** -50, 2.0 ** -51, 1e-40, 0.0, 3e38, 1.5]
+    if special:
+        spec += [np.inf, np.nan]
+    n_spec = len(spec)
+    n_cols = 4096
+
+    def logu(k, lo=-149.0, hi=127.0):
+        mag = np.exp2(rng.uniform(lo, hi, k))
+        return (mag * np.where(rng.random(k) < 0.5, -1.0, 1.0)).astype(np.float32)
+
+    x = np.empty(n_cols, np.float32)
+    x[:n_spec] = np.array(spec, np.float64).astype(np.float32)
+    wild_lo, wild_hi, tiny_hi = n_spec, 1024, 1280
+    x[wild_lo:wild_hi] = logu(wild_hi - wild_lo)
+    x[wild_hi:tiny_hi] = logu(tiny_hi - wild_hi, -149.0, -50.0)
+    x[tiny_hi:] = rng.uniform(-1.0, 1.0, n_cols - tiny_hi).astype(np.float32)
+    rows = [
+        [(0, 1e20)], [(0, 1e20), (1, 1e20)], [(2, 1e-25)], [(2, 1e-25), (3, 1e-25)],
+        [(4, 1.0), (2, 1e-25)], [(5, 1.8e19), (5, 1.8e19)], [(6, 2.0 ** -50)], [(7, 2.0 ** -50)],
+        [(8, 1.0)], [(9, 1e-30)], [(2, 0.0)], [(10, 3e38), (10, -3e38)], [(11, 1.5)] * 20, [],
+        [(4, 1.0), (0, 1e20), (1, 1e20), (4, -1.0)], [(8, 1e-5), (2, 1e-25), (6, 2.0 ** -60)],
+    ]
+    if special:
+        rows += [[(12, 1.0)], [(12, 0.0)], [(13, 2.0)], [(4, 1.0), (12, -1.0), (12, 1.0)]]
+    for _ in range(n_wild):
+        k = int(rng.integers(1, 41))
+        cols = rng.integers(wild_lo, wild_hi, k)
+        rows.append(list(zip(cols.tolist(), logu(k).tolist())))
+    for _ in range(n_wild // 2):  # every product below 2^-100
+        k = int(rng.integers(1, 41))
+        cols = rng.integers(wild_hi, tiny_hi, k)
+        rows.append(list(zip(cols.tolist(), logu(k, -149.0, -50.0).tolist())))
+    cols = rng.integers(wild_lo, wild_hi, long_len)
+    rows.append(list(zip(cols.tolist(), logu(long_len).tolist())))
+    for _ in range(n_normal):
+        k = int(rng.integers(1, 25))
+        cols = rng.integers(tiny_hi, n_cols, k)
+        rows.append(list(zip(cols.tolist(), rng.standard_normal(k).tolist())))
+    order = rng.permutation(len(rows))
+    rows = [rows[i] for i in order]
+    counts = np.array([len(r) for r in rows], np.int64)
+    rp = _row_ptr_from_counts(counts)
+    col = np.array([c for r in rows for c, _ in r], np.int32)
+    val = np.array([v for r in rows for _, v in r], np.float64).astype(np.float32)
+    return CRS(rp, col, val, n_cols), x
+
+
+def column_heavy_csr(n_rows: int, n_cols: int, seed: int, dense: int = 1, medium: int = 50,
+                     medium_len: int = 2000, max_len: int = 6) -> CRS:
+    """Irregular CRS with long columns (for the transposed build): ``dense``
+    columns with an entry in every row, ``medium`` columns with about
+    ``medium_len`` entries each (rows drawn at random), and up to ``max_len``
+    random other entries per row; columns unsorted within rows, N(0,1) values."""
+    rng = np.random.default_rng(seed)
+    dense_cols = rng.choice(n_cols, size=min(dense, n_cols), replace=False)
+    med_cols = rng.choice(n_cols, size=min(medium, n_cols), replace=False)
+    per_row = [[] for _ in range(n_rows)]
+    for c in dense_cols.tolist():
+        for i in range(n_rows):
+            per_row[i].append(c)
+    for c in med_cols.tolist():
+        for i in rng.integers(0, n_rows, min(medium_len, n_rows)).tolist():
+            per_row[i].append(c)
+    lens = rng.integers(0, max_len + 1, n_rows)
+    for i in range(n_rows):
+        per_row[i].extend(rng.integers(0, n_cols, int(lens[i])).tolist())
+        rng.shuffle(per_row[i])
+    counts = np.array([len(r) for r in per_row], np.int64)
+    rp = _row_ptr_from_counts(counts)
+    col = np.array([c for r in per_row for c in r], np.int32)
+    return CRS(rp, col, rng.standard_normal(col.size), n_cols)

@@ -82,6 +82,41 @@ def test_transpose_structure_bitexact(shape):
     assert_bitexact(perm, operm, "perm")
 
 
+@pytest.mark.parametrize("case", ["dense_column", "medium_columns", "all_one_column"])
+def test_transpose_long_columns(case):
+    """Long columns of A (long rows of A^T): one column with an entry in each of
+    100,000 rows, or 200 columns of about 3000 entries, or every entry in one
+    column; the structure is bit-exact against the oracle (the column order is a
+    stable radix sort, linear in the entries), and grad_x = A^T g on it is
+    within the bound (first pass through the permutation, second on the
+    laid-out copy)."""
+    import time
+    if case == "dense_column":
+        A = W.column_heavy_csr(100000, 50000, seed=5, dense=1, medium=0)
+    elif case == "medium_columns":
+        A = W.column_heavy_csr(60000, 40000, seed=6, dense=0, medium=200, medium_len=3000)
+    else:
+        n = 70000
+        A = W.CRS(np.arange(n + 1, dtype=np.int32), np.full(n, 123, np.int32), W.uniform(n, 7), 500)
+    M = make(A)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rpt, cit, perm = M.transpose_structure()
+    build_s = time.perf_counter() - t0
+    ort, oct_, operm = oracle.transpose(A.row_ptr, A.col_idx, A.n_cols)
+    assert_bitexact(rpt, ort, "rowT_ptr")
+    assert_bitexact(cit, oct_, "colT")
+    assert_bitexact(perm, operm, "perm")
+    assert build_s < 5.0, build_s
+    x = W.uniform(A.n_cols, 8)
+    g = W.uniform(A.n_rows, 9)
+    rgx, rgv, bound = oracle.backward(*A.astuple(), A.n_cols, g, x, with_bound=True)
+    for _ in range(2):
+        gx, gv = M.backward(dev(g), dev(x))
+        assert_within(host(gx), rgx, bound, 1e-13, f"grad_x {case}")
+        assert_bitexact(host(gv), rgv, f"grad_val {case}")
+
+
 @pytest.mark.parametrize("alpha", [1.0, -0.5])
 def test_backward_small(alpha):
     A = W.random_csr(3000, 2500, seed=9, max_len=30, long_rows=2, long_len=4500)
@@ -133,6 +168,17 @@ def st27():
     return W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
 
 
+@pytest.mark.parametrize("nrhs", [4, 8, 16, 32])
+def test_block_vectors_27pt_128(st27, nrhs):
+    """Block vectors on the full 128^3 27-point matrix (row slices, groups of 4),
+    every row of Y against the oracle."""
+    A = st27
+    M = make(A)
+    X = W.uniform(0, W.SEED_BLOCK_X + nrhs, shape=(A.n_cols, nrhs))
+    ref, bound = oracle.spmm(*A.astuple(), X, with_bound=True)
+    assert_within(host(M.spmm(dev(X))).ravel(), ref.ravel(), bound.ravel(), 1e-13, f"27-point nrhs={nrhs}")
+
+
 def test_backward_27pt_128(st27):
     A = st27
     assert (A.n_rows, A.nnz) == (2097152, 55742968)
@@ -167,6 +213,46 @@ def test_backward_27pt_fp32(st27):
         gx, gv = M.backward(dev(g), dev(x))
         assert_within(host(gx), rgx, gbound, 1e-6, f"27-point fp32 grad_x pass {rep}")
         assert_within(host(gv), rgv, np.abs(rgv), 1e-6, f"27-point fp32 grad_val pass {rep}")
+
+
+def test_fd_16cubed_fp32_storage():
+    """The FP32-storage reverse pass on the 16^3 27-point instance against central
+    differences of f = g^T A(val) x computed by the library's own FP32-storage
+    forward product (FP64 result): f is linear in each value and each x entry, so
+    the quotient over the perturbation actually stored in FP32 is exact up to the
+    forward product's rounding.  Also against the oracle's reverse pass."""
+    A = W.stencil27(W.STENCIL27_FD_GRID, seed=W.SEED_STENCIL27_VAL)
+    v32 = A.val.astype(np.float32)
+    x32 = W.uniform(A.n_cols, W.SEED_STENCIL27_X).astype(np.float32)
+    g32 = W.uniform(A.n_rows, W.SEED_STENCIL27_G).astype(np.float32)
+    from paper_1106_5908_gb300 import Matrix
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
+    gd = dev(g32).double()
+    for alpha in (1.0, 1.25):
+        M.set_values(dev(v32))
+        gx, gv = M.backward(dev(g32), dev(x32), alpha)
+        gx, gv = host(gx).astype(np.float64), host(gv).astype(np.float64)
+        rgx, rgv, gb = oracle.backward(A.row_ptr, A.col_idx, v32.astype(np.float64), A.n_cols,
+                                       g32.astype(np.float64), x32.astype(np.float64), alpha, with_bound=True)
+        assert_within(gx, rgx, gb, 1e-6, "fp32 grad_x vs oracle")
+        assert_within(gv, rgv, np.abs(rgv), 1e-6, "fp32 grad_val vs oracle")
+
+        def f(vals, xx):
+            M.set_values(dev(vals))
+            return alpha * torch.dot(gd, M.apply(dev(xx), out_dtype=torch.float64)).item()
+
+        rng = np.random.default_rng(1)
+        h = np.float32(1e-2)
+        for k in rng.choice(A.nnz, 12, replace=False):
+            vp = v32.copy(); vp[k] = v32[k] + h
+            vm = v32.copy(); vm[k] = v32[k] - h
+            fd = (f(vp, x32) - f(vm, x32)) / (float(vp[k]) - float(vm[k]))
+            assert fd == pytest.approx(gv[k], rel=1e-6, abs=1e-9), ("val", k)
+        for j in rng.choice(A.n_cols, 12, replace=False):
+            xp = x32.copy(); xp[j] = x32[j] + h
+            xm = x32.copy(); xm[j] = x32[j] - h
+            fd = (f(v32, xp) - f(v32, xm)) / (float(xp[j]) - float(xm[j]))
+            assert fd == pytest.approx(gx[j], rel=1e-6, abs=1e-6 * gb[j] + 1e-9), ("x", j)
 
 
 def test_autograd_fd_16cubed():
@@ -272,31 +358,37 @@ def test_batched_small(dtype):
             assert_within(host(yd[m]), ref, bound, rel, f"batch m={m} rep={rep}")
 
 
-def test_batched_256_full_size():
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_256_full_size(dtype):
     """The benchmark's batch at full size: 256 matrices, N ~ U[1000, 200000]
-    (5-point Laplacians and Hamiltonian-like patterns, 235 M entries), one
-    persistent launch replayed from a CUDA graph; every result against the
-    oracle, for two right-hand sides (the second replay reuses the graph)."""
+    (5-point Laplacians and Hamiltonian-like patterns, 235 M entries), FP64 and
+    FP32 storage, one persistent launch replayed from a CUDA graph; every result
+    against the oracle, for two right-hand sides (the second replay reuses the
+    graph)."""
     from paper_1106_5908_gb300 import Batch, Matrix
+    npdt = np.float32 if dtype == "f32" else np.float64
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    rel = 1e-6 if dtype == "f32" else 1e-13
     sizes = W.batch_sizes(W.BATCH_COUNT)
     As, mats = [], []
     for m, n in enumerate(sizes):
         A = W.batch_matrix(m, int(n))
         As.append(A)
-        mats.append(Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols))
+        mats.append(Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(npdt), A.n_cols))
     assert len(As) == 256 and sum(A.nnz for A in As) > 2e8
     B = Batch(mats)
-    ys = [torch.empty(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
-    xd = [torch.empty(A.n_cols, dtype=torch.float64, device="cuda") for A in As]
+    ys = [torch.empty(A.n_rows, dtype=tdt, device="cuda") for A in As]
+    xd = [torch.empty(A.n_cols, dtype=tdt, device="cuda") for A in As]
     for rep in range(2):  # same buffers: the second apply replays the captured graph
-        xs = [W.uniform(A.n_cols, 1000 * rep + m) for m, A in enumerate(As)]
+        xs = [W.uniform(A.n_cols, 1000 * rep + m).astype(npdt) for m, A in enumerate(As)]
         for m in range(len(As)):
             xd[m].copy_(torch.as_tensor(xs[m]))
         B.apply(xd, ys)
         torch.cuda.synchronize()
         for m, A in enumerate(As):
-            ref, bound = oracle.spmv(*A.astuple(), xs[m], with_bound=True)
-            assert_within(host(ys[m]), ref, bound, 1e-13, f"batch m={m} rep={rep}")
+            ref, bound = oracle.spmv(A.row_ptr, A.col_idx, A.val.astype(npdt).astype(np.float64),
+                                     xs[m].astype(np.float64), with_bound=True)
+            assert_within(host(ys[m]), ref, bound, rel, f"batch {dtype} m={m} rep={rep}")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

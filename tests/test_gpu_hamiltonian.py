@@ -164,15 +164,51 @@ def test_hamiltonian_fp32_storage(ham, acc):
 
 @pytest.mark.parametrize("nrhs", [4, 8, 16, 32])
 def test_hamiltonian_block_vectors(ham, m_ham, nrhs):
+    """Block vectors on the full matrix, every row of Y against the oracle."""
     A, _, _, _ = ham
     X = W.uniform(0, W.SEED_BLOCK_X, shape=(A.n_rows, nrhs))
     Y = host(m_ham.spmm(dev(X)))
-    rng = np.random.default_rng(nrhs)
-    rows = np.sort(rng.choice(A.n_rows, 4000, replace=False))
-    # oracle on the sampled rows (a sub-CRS with the same entries)
-    lens = np.diff(A.row_ptr)[rows]
-    rp = np.zeros(rows.size + 1, np.int64)
-    np.cumsum(lens, out=rp[1:])
-    idx = np.concatenate([np.arange(A.row_ptr[r], A.row_ptr[r + 1]) for r in rows])
-    ref, bound = oracle.spmm(rp.astype(np.int32), A.col_idx[idx], A.val[idx], X, with_bound=True)
-    assert_within(Y[rows].ravel(), ref.ravel(), bound.ravel(), 1e-13, f"Hamiltonian nrhs={nrhs}")
+    ref, bound = oracle.spmm(*A.astuple(), X, with_bound=True)
+    assert_within(Y.ravel(), ref.ravel(), bound.ravel(), 1e-13, f"Hamiltonian nrhs={nrhs}")
+    # alpha/beta form on the same launch shape
+    Y0 = W.uniform(0, 5, shape=(A.n_rows, nrhs))
+    ref2, bound2 = oracle.spmm(*A.astuple(), X, -0.5, 2.0, Y0, with_bound=True)
+    Yd = dev(Y0)
+    m_ham.spmm(dev(X), Yd, -0.5, 2.0)
+    assert_within(host(Yd).ravel(), ref2.ravel(), bound2.ravel(), 1e-13, f"Hamiltonian nrhs={nrhs} a/b")
+
+
+@pytest.fixture(scope="module")
+def reorderings(ham):
+    A = ham[0]
+    return {"rcm": W.rcm_order(A), "random": W.random_order(A.n_rows)}
+
+
+@pytest.mark.parametrize("order", ["rcm", "random"])
+def test_hamiltonian_reordered(ham, reorderings, order):
+    """The ordering study's matrices (P A P^T in reverse Cuthill-McKee and in a
+    random order, x permuted alike) through the autotuned plan, the row-slice
+    plan, the split form and FP32 storage, against the oracle on the permuted
+    matrix; the permuted product is the natural one permuted."""
+    from paper_1106_5908_gb300 import Matrix
+    A, x, ref_nat, _ = ham
+    p = reorderings[order]
+    B = W.permute_symmetric(A, p)
+    xp = x[p]
+    ref, bound = oracle.spmv(*B.astuple(), xp, with_bound=True)
+    assert np.all(np.abs(ref - ref_nat[p]) <= 1e-13 * bound)
+    M = Matrix.from_csr(B.row_ptr, B.col_idx, B.val, B.n_cols)
+    info = M.info()
+    assert_within(host(M.apply(dev(xp))), ref, bound, 1e-13, f"{order} auto {info['family']},{info['E']}")
+    for plan in ((4, 7), (5, 4096)):
+        M.set_plan(*plan)
+        assert_within(host(M.apply(dev(xp))), ref, bound, 1e-13, f"{order} plan {plan}")
+    sp = M.split(8)
+    y = sp.apply(dev(xp), s_comm=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    assert_within(host(y), ref, bound, 1e-13, f"{order} split")
+    v32 = B.val.astype(np.float32)
+    x32 = xp.astype(np.float32)
+    M32 = Matrix.from_csr(B.row_ptr, B.col_idx, v32, B.n_cols)
+    r32, b32 = oracle.spmv(B.row_ptr, B.col_idx, v32.astype(np.float64), x32.astype(np.float64), with_bound=True)
+    assert_within(host(M32.apply(dev(x32))), r32, b32, 1e-6, f"{order} FP32")

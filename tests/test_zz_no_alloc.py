@@ -1,16 +1,20 @@
 """GPU test of spmv_transpose_noalloc, the transposed-CRS build that allocates no
-device memory (for callers that cannot call cudaMalloc: inside a CUDA graph
-capture, in latency-bound loops, or with device memory reserved elsewhere).
+device memory (for callers that cannot call cudaMalloc: latency-bound loops
+that must not wait on the allocator, or programs whose device memory is
+reserved by another allocator).
 
 Its output is compared bit for bit with the existing entry point
-spmv_get_transpose on two calls in a row with different matrices, so the second
-call runs on the scratch array the first one left behind.  The file name makes
-pytest collect it last; it passes on its own in a fresh process as well."""
+spmv_get_transpose and with the oracle's transposed CRS on calls in a row with
+different matrices, so each call after the first runs on the scratch array the
+previous one left behind; long columns (one column with an entry in every row)
+are among them.  The file name makes pytest collect it last; it passes on its
+own in a fresh process as well."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1106_5908_gb300 import workloads as W
 from gpu_util import need_gpu
 
@@ -44,12 +48,15 @@ def test_noalloc_transpose_matches_existing_on_two_calls():
     need_gpu()
     first = W.random_csr(3000, 2600, seed=31, max_len=40, long_rows=2, long_len=2000)
     second = W.hamiltonian_like(20000, seed=32)
-    for A in (first, second, first):
+    third = W.column_heavy_csr(100000, 60000, seed=33, dense=1, medium=20, medium_len=3000)
+    for A in (first, second, third, first):
         ref = existing_transpose(A)
+        orc = oracle.transpose(A.row_ptr, A.col_idx, A.n_cols)
         got = noalloc_transpose(A)
-        for name, g, r in zip(("rowT_ptr", "colT_idx", "perm"), got, ref):
-            assert g.shape == r.shape, name
+        for name, g, r, o in zip(("rowT_ptr", "colT_idx", "perm"), got, ref, orc):
+            assert g.shape == r.shape == o.shape, name
             assert np.array_equal(g, r), name
+            assert np.array_equal(g, o), name
 
 
 def test_noalloc_transpose_rejects_too_many_columns():
