@@ -45,8 +45,8 @@ FP64_FMA_PER_S = 598e9
 # DRAM traffic of one launch of the plain FP64 chunk kernel on this workload, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_hash": "9b7fdf6e19def671", "bytes_per_launch": 751066880,
-           "source": "profiles/k_slot_f64_hamiltonian_4194304.md (mean of 3 launches)"}
+TRAFFIC = {"kernel_hash": "87a96c5fe6f5910d", "bytes_per_launch": 753408256,
+           "source": "profiles/k_slot_f64_hamiltonian_4194304.md (one launch, --set full)"}
 
 
 def kernel_hash() -> str:
@@ -630,16 +630,17 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
 
 
 def run_only_plain(args, local_rank):
-    """Only the plain FP64 product, warm-up plus K launches (the case a kernel
-    profiler captures): on the Hamiltonian-like matrix (`--only plain`), the
-    160^3 7-point Poisson matrix (`--only poisson7`) or the 128^3 27-point
-    stencil (`--only stencil27`)."""
+    """Only the plain product, warm-up plus K launches (the case a kernel profiler
+    captures): on the Hamiltonian-like matrix (`--only plain`, FP64; `--only
+    plain32`, FP32 storage), the 160^3 7-point Poisson matrix (`--only
+    poisson7`) or the 128^3 27-point stencil (`--only stencil27`)."""
     import torch
     from paper_1106_5908_gb300 import Matrix
     from paper_1106_5908_gb300.build import build as build_lib
     torch.cuda.set_device(local_rank)
     build_lib()
-    if args.only == "plain":
+    f32 = args.only == "plain32"
+    if args.only in ("plain", "plain32"):
         A, x = hamiltonian_workload()
     elif args.only == "poisson7":
         A = W.laplace3d(W.POISSON7_GRID)
@@ -647,9 +648,9 @@ def run_only_plain(args, local_rank):
     else:
         A = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
         x = W.uniform(A.n_cols, W.SEED_STENCIL27_X)
-    M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
-    xd = torch.as_tensor(x).cuda()
-    y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+    M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val.astype(np.float32) if f32 else A.val, A.n_cols)
+    xd = torch.as_tensor(x.astype(np.float32) if f32 else x).cuda()
+    y = torch.empty(A.n_rows, dtype=xd.dtype, device="cuda")
     for _ in range(args.warmup):
         M.apply(xd, y)
     torch.cuda.synchronize()
@@ -661,8 +662,11 @@ def run_only_plain(args, local_rank):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"only": f"{args.only}_f64", "n": A.n_rows, "nnz": A.nnz, "ms_per_launch": ms, "plan": M.info(),
-                      "GBs": model.bytes_plain(A.n_rows, A.n_cols, A.nnz) / ms / 1e6}), flush=True)
+    vb = 4 if f32 else 8
+    print(json.dumps({"only": args.only if f32 else f"{args.only}_f64", "n": A.n_rows, "nnz": A.nnz,
+                      "ms_per_launch": ms, "plan": M.info(),
+                      "GBs": model.bytes_plain(A.n_rows, A.n_cols, A.nnz, val_bytes=vb, x_bytes=vb, y_bytes=vb)
+                      / ms / 1e6}), flush=True)
 
 
 def run_ordering_study(args, local_rank):
@@ -726,9 +730,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=("plain", "poisson7", "stencil27"), default=None,
-                    help="run only the plain FP64 product on the Hamiltonian-like matrix, the 7-point "
-                         "or the 27-point matrix (for kernel profiling)")
+    ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "stencil27"), default=None,
+                    help="run only the plain FP64 product on the Hamiltonian-like matrix (plain32: its "
+                         "FP32-storage product), the 7-point or the 27-point matrix (for kernel profiling)")
     ap.add_argument("--study", choices=("ordering",), default=None,
                     help="natural / RCM / random ordering of the Hamiltonian-like matrix")
     ap.add_argument("--study-auto-only", action="store_true",

@@ -112,7 +112,7 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7, 11, 15;
  * family 4: slot-major warp-chunk kernel (values and column indices copied once
  *           into chunk-major, lane-interleaved order and loaded coalesced into
- *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 15);
+ *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 9, 15);
  *           the copy is built on first use and its values follow spmv_set_values;
  * family 5: sorted row-slice kernel (SELL-C-sigma with C = 64: in each window
  *           of param rows, a power of two from 32 to 2^20, default 4096, the
@@ -120,7 +120,14 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  *           lane; rows of more than 128 entries summed by a whole warp); FP64
  *           and FP32 storage with float-float accumulation, other combinations
  *           run the slot-major kernel; copy built on first use, values follow
- *           spmv_set_values.
+ *           spmv_set_values;
+ * family 6: the slot-major kernel of family 4 with each chunk's values brought
+ *           into a two-stage shared-memory ring per warp by 1-D bulk copies
+ *           (cp.async.bulk) instead of register loads, so they bypass L1's miss
+ *           handling; E = 7, 9 (FP64), 9, 15 (FP32 storage, float-float); FP64
+ *           and FP32 vectors of the storage type, other combinations and the
+ *           split form's row-mapped parts run family 4.  A bounded wait that
+ *           gives up records a timeout (spmv_check_device_error).
  * param 0 keeps a default.  Results are unchanged up to summation order. */
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 

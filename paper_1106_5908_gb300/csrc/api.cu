@@ -843,9 +843,26 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
             return lops.launch(lp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
         }
     }
+    if (h->family == 6 && !h->d_rmap) {
+        SlotOps tops;
+        SlotTable *tt = nullptr;
+        if (slot_ops_tv(h->vk, xk, yk, acc, h->E, &tops) && (tt = get_slots(h, h->E, s)) != nullptr) {
+            SlotParams sp{};
+            sp.chunks = tt->d;
+            sp.lmask = tt->lmask;
+            sp.vals = tt->vals;
+            sp.cols = tt->cols;
+            sp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
+            sp.n_chunks = tt->n;
+            sp.alpha = alpha;
+            sp.beta = beta;
+            sp.err = h->d_err;
+            return tops.launch(sp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+        }
+    }
     SlotOps sops;
     SlotTable *t = nullptr;
-    if ((h->family == 4 || h->family == 5) &&
+    if ((h->family == 4 || h->family == 5 || h->family == 6) &&
         ((h->d_rmap && slot_ops(h->vk, xk, yk, acc, h->E, true, &sops)) ||
          slot_ops(h->vk, xk, yk, acc, h->E, false, &sops)) &&
         (t = get_slots(h, h->E, s)) != nullptr) {
@@ -858,15 +875,16 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
         sp.n_chunks = t->n;
         sp.alpha = alpha;
         sp.beta = beta;
+        sp.err = h->d_err;
         return sops.launch(sp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     }
     // the staged chunk kernels (also families 4 and 5 in the vector and
     // accumulator combinations their kernels are not compiled for, FP32 storage
     // with an FP64 result or FP64 accumulation, and when their copies could not
     // be allocated)
-    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->d_rmap) {
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->family == 6 || h->d_rmap) {
         int E = h->E;
-        if ((h->family == 4 || h->family == 5) && E != 7 && E != 15) E = 15;
+        if ((h->family == 4 || h->family == 5 || h->family == 6) && E != 7 && E != 15) E = 15;
         WarpOps ops;
         // family 3 selects the three-stage kernel of the same chunking
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
@@ -1000,12 +1018,14 @@ static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     if (h->family == 5 && !h->d_rmap && sell_ops(h->vk, xk, yk, acc, &lops) && get_sell(h, h->sigma, nullptr))
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     SlotOps sops;
-    if ((h->family == 4 || h->family == 5) && slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops) &&
+    if ((h->family == 4 || h->family == 5 || h->family == 6) &&
+        (slot_ops(h->vk, xk, yk, acc, h->E, h->d_rmap != nullptr, &sops) ||
+         (h->family == 6 && !h->d_rmap && slot_ops_tv(h->vk, xk, yk, acc, h->E, &sops))) &&
         get_slots(h, h->E, nullptr))
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
-    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->d_rmap) {
+    if (h->family == 0 || h->family == 3 || h->family == 4 || h->family == 5 || h->family == 6 || h->d_rmap) {
         int E = h->E;
-        if ((h->family == 4 || h->family == 5) && E != 7 && E != 15) E = 15;
+        if ((h->family == 4 || h->family == 5 || h->family == 6) && E != 7 && E != 15) E = 15;
         WarpOps ops;
         const bool ok3 = h->family == 3 && warp_ops(h->vk, xk, yk, acc, E + 100, false, false, &ops);
         if (!ok3 && !warp_ops(h->vk, xk, yk, acc, E, false, false, &ops)) E = 16;
@@ -1132,7 +1152,7 @@ spmv_status spmv_get_info(spmv_handle h, int32_t *n_rows, int32_t *n_cols, int64
             E = h->sigma;
             rowcap = kSellC;
             if (cudaDeviceSynchronize() != cudaSuccess) return SPMV_ERR_CUDA;
-        } else if (h->family == 4) {
+        } else if (h->family == 4 || h->family == 6) {
             SlotTable *t = get_slots(h, E, nullptr);
             if (t) {
                 nunits = t->n;
@@ -1174,7 +1194,15 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts) {
 }
 
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
-    if (!h || family < 0 || family > 5) return SPMV_ERR_INVALID_ARG;
+    if (!h || family < 0 || family > 6) return SPMV_ERR_INVALID_ARG;
+    if (family == 6) {
+        const bool f64 = h->vk == kF64;
+        if (param != 0 && !(f64 ? (param == 7 || param == 9) : (param == 9 || param == 15)))
+            return SPMV_ERR_INVALID_ARG;
+        h->family = 6;
+        h->E = param ? param : 9;
+        return SPMV_OK;
+    }
     if (family == 5) {
         if (param != 0 && (param < 32 || param > (1 << 20) || (param & (param - 1)))) return SPMV_ERR_INVALID_ARG;
         h->family = 5;
@@ -1615,6 +1643,7 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
                 sp.n_chunks = t->n;
                 sp.alpha = alpha;
                 sp.beta = 0.0;
+                sp.err = h->d_err;
                 if (sops.launch(sp, s) != cudaSuccess) return SPMV_ERR_CUDA;
                 done = true;
             }

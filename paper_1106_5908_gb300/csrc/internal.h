@@ -43,6 +43,9 @@ struct SlotOps {
 // pre: the variant that loads each chunk's row map and old y before its chains
 // (row-mapped products).
 bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops);
+// The variant whose values arrive by bulk copies into a shared-memory ring
+// (plan family 6): FP64 E = 7, 9; FP32 float-float E = 9, 15.
+bool slot_ops_tv(int vk, int xk, int yk, int acc, int E, SlotOps *ops);
 // The batched variant (vectors of the value type): FP64, FP32 float-float; E = 7.
 bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops);
 // Slot-major copies of the values (and, when cols_out is not null, the column

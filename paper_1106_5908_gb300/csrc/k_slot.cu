@@ -52,6 +52,18 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     return false;
 }
 
+bool slot_ops_tv(int vk, int xk, int yk, int acc, int E, SlotOps *ops) {
+    if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64) {
+        if (E == 7) { ops->launch = &SlotKernelTV<7, double, double, double, AccF64>::launch; return true; }
+        if (E == 9) { ops->launch = &SlotKernelTV<9, double, double, double, AccF64>::launch; return true; }
+    }
+    if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF) {
+        if (E == 9) { ops->launch = &SlotKernelTV<9, float, float, float, AccFF>::launch; return true; }
+        if (E == 15) { ops->launch = &SlotKernelTV<15, float, float, float, AccFF>::launch; return true; }
+    }
+    return false;
+}
+
 cudaError_t launch_slot_relayout(const void *chunks, int E, int64_t n_slots, int vk, const void *val,
                                  const int32_t *col, void *vals_out, int32_t *cols_out, cudaStream_t s) {
     if (n_slots <= 0) return cudaSuccess;

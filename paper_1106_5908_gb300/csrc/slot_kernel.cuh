@@ -34,6 +34,7 @@ struct SlotParams {
     const int32_t *cmat;
     int32_t n_chunks;
     double alpha, beta;
+    int32_t *err;           // device error word (the staged variant's bounded waits)
 };
 
 __device__ __forceinline__ double ld_stream(const double *p, uint64_t pol) {
@@ -212,6 +213,185 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         }
     }
 }
+
+// Staged-values variant (TV).  The values of each chunk (32E contiguous
+// elements of the slot-major copy) arrive by one 1-D bulk copy (cp.async.bulk,
+// evict-first in L2) into a two-stage ring per warp in shared memory, requested
+// two chunks before they are used; the column indices and the x gathers stay
+// plain loads one and two chunks ahead, as above.  What this changes: the
+// streamed values no longer pass through L1's miss handling, which on the
+// Hamiltonian-like matrix limits the kernel (about one missed sector per cycle
+// per SM, shared by the streamed operands and the gathers of far columns), and
+// the values no longer occupy registers while they are in flight.  Every wait
+// on a stage is bounded (mbar_wait_bounded); on a timeout the warp records
+// kDevErrTimeout, waits (bounded) for its other stage and leaves.
+template <int E, typename VT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256, 2) k_slot_tv(const SlotParams p) {
+    constexpr int SL = 32 * E;
+    constexpr uint32_t kStageBytes = SL * sizeof(VT);
+    static_assert(kStageBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
+    __shared__ ACC s_rows[8][kWarpRowCap];
+    __shared__ __align__(128) VT s_vals[8][2][SL];
+    __shared__ __align__(8) uint64_t s_bar[8][2];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * 8;
+    const int n = p.n_chunks;
+    int c = blockIdx.x * 8 + wib;
+    if (lane == 0) {
+        mbar_init(&s_bar[wib][0], 1);
+        mbar_init(&s_bar[wib][1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (c >= n) return;
+    ACC *srow = s_rows[wib];
+    const uint64_t pol = l2_evict_first_policy();
+    const VT *__restrict__ vals = static_cast<const VT *>(p.vals);
+    const double alpha = p.alpha, beta = p.beta;
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+    const XT *__restrict__ x = static_cast<const XT *>(p.m.x);
+    YT *__restrict__ y = static_cast<YT *>(p.m.y);
+    const MatRef m = p.m;
+
+    auto regular = [](const ChunkDesc &d) { return (d.r1f & (kChunkLong | kChunkEmpty)) == 0; };
+    auto hi_of = [&](const ChunkDesc &d) { return max(0, min(E, d.k1 - d.k0 - lane * E)); };
+    auto load_cols = [&](int cc, int32_t (&cl)[E]) {
+        const int32_t *b = p.cols + static_cast<int64_t>(cc) * SL + lane;
+#pragma unroll
+        for (int e = 0; e < E; ++e) cl[e] = ld_stream(b + e * 32, pol);
+    };
+    auto gather = [&](const ChunkDesc &d, const int32_t (&cl)[E], XT (&xv)[E]) {
+        const int hi = regular(d) ? hi_of(d) : 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) xv[e] = (e < hi) ? __ldg(x + cl[e]) : XT(0);
+    };
+    auto load_desc = [&](int cc) {
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(p.chunks) + cc);
+        return ChunkDesc{q.x, q.y, q.z, q.w};
+    };
+    // lane 0 requests the values of chunk cc into stage st (every lane has
+    // finished reading that stage: the caller synchronises the warp first)
+    auto request = [&](int cc, int st) {
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar[wib][st], kStageBytes);
+            bulk_g2s(&s_vals[wib][st][0], vals + static_cast<int64_t>(cc) * SL, kStageBytes, &s_bar[wib][st], pol);
+        }
+    };
+    uint32_t phase = 0;  // bit st: parity of the next completion of stage st
+
+    request(c, 0);
+    if (c + nwarps < n) request(c + nwarps, 1);
+    ChunkDesc dc = load_desc(c);
+    uint32_t mc = __ldg(p.lmask + static_cast<int64_t>(c) * 32 + lane);
+    XT xc[E];
+    {
+        int32_t cl[E];
+        load_cols(c, cl);
+        gather(dc, cl, xc);
+    }
+    ChunkDesc dn{};
+    uint32_t mn = 0;
+    int32_t cn[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) cn[e] = 0;
+    if (c + nwarps < n) {
+        dn = load_desc(c + nwarps);
+        mn = __ldg(p.lmask + static_cast<int64_t>(c + nwarps) * 32 + lane);
+        load_cols(c + nwarps, cn);
+    }
+
+    for (int it = 0; c < n; c += nwarps, ++it) {
+        const int st = it & 1;
+        const int c1 = c + nwarps, c2 = c + 2 * nwarps;
+        // chunk c1: gathers; chunk c2: descriptor, row starts, columns
+        XT xn[E];
+        if (c1 < n) {
+            gather(dn, cn, xn);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) xn[e] = XT(0);
+        }
+        ChunkDesc d2{};
+        uint32_t m2 = 0;
+        int32_t c2l[E];
+        if (c2 < n) {
+            d2 = load_desc(c2);
+            m2 = __ldg(p.lmask + static_cast<int64_t>(c2) * 32 + lane);
+            load_cols(c2, c2l);
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) c2l[e] = 0;
+        }
+        // ---- chunk c: its values from stage st --------------------------------
+        const bool ok = mbar_wait_bounded(&s_bar[wib][st], (phase >> st) & 1u);
+        phase ^= 1u << st;
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) set_error(p.err, kDevErrTimeout);
+            if (c1 < n) (void)mbar_wait_bounded(&s_bar[wib][st ^ 1], (phase >> (st ^ 1)) & 1u);
+            return;
+        }
+        VT vc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) vc[e] = s_vals[wib][st][e * 32 + lane];
+        __syncwarp();
+        if (c2 < n) request(c2, st);
+        const int r0 = dc.r0;
+        const int r1 = dc.r1f & kChunkRowMask;
+        if (dc.r1f & kChunkLong) {
+            long_row<VT, XT, YT, ACC, false>(m, dc, x, y, alpha, beta, plain, lane);
+        } else if (dc.r1f & kChunkEmpty) {
+            rows_per_lane<VT, XT, YT, ACC, false>(m, r0, r1, x, y, alpha, beta, plain, lane);
+        } else {
+            const int hi = hi_of(dc);
+            const uint32_t mbits = mc & ((1u << E) - 1u);
+            chunk_lane_pre<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, (mc & kSlotEnds) != 0u,
+                                           static_cast<int>((mc >> kSlotPreShift) & kSlotPreMask), r0, srow, lane);
+            __syncwarp();
+            for (int q = lane; q < r1 - r0; q += 32)
+                store_acc<VT, false>(m, x, y, r0 + q, srow[q], alpha, beta, plain);
+        }
+        __syncwarp();  // the row buffer is free again
+        dc = dn;
+        mc = mn;
+        dn = d2;
+        mn = m2;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            xc[e] = xn[e];
+            cn[e] = c2l[e];
+        }
+    }
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC>
+struct SlotKernelTV {
+    static int grid_limit() {
+        static int cached = -1;
+        static int cached_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cached >= 0 && cached_dev == dev) return cached;
+        int per_sm = 0, sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot_tv<E, VT, XT, YT, ACC>, 256, 0) !=
+            cudaSuccess)
+            return 0;
+        cached = per_sm * sms;
+        cached_dev = dev;
+        return cached;
+    }
+    static cudaError_t launch(const SlotParams &p, cudaStream_t s) {
+        if (p.n_chunks <= 0) return cudaSuccess;
+        const int lim = grid_limit();
+        if (lim <= 0) return cudaErrorInvalidConfiguration;
+        const int want = (p.n_chunks + 7) / 8;
+        k_slot_tv<E, VT, XT, YT, ACC><<<want < lim ? want : lim, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+};
 
 // Slot-major copies of a CRS: slot t = chunk*32E + e*32 + l holds entry
 // k0 + l*E + e of the chunk when the chunk is regular and the entry belongs to

@@ -23,8 +23,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 15), (0, 7), (3, 15), (4, 7), (4, 9), (4, 15), (5, 32), (5, 256), (5, 4096), (0, 16), (2, 15),
-         (2, 31), (1, 1), (1, 4), (1, 32)]
+PLANS = [(6, 9), (6, 15), (0, 15), (0, 7), (3, 15), (4, 7), (4, 9), (4, 15), (5, 32), (5, 256), (5, 4096), (0, 16),
+         (2, 15), (2, 31), (1, 1), (1, 4), (1, 32)]
 FORMS = [(1.0, 0.0), (-0.75, 1.0), (2.0, -0.5), (1.0, 1.0)]
 
 

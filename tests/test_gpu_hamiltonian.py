@@ -47,8 +47,8 @@ def test_hamiltonian_plain_f64(ham, m_ham):
     assert_within(host(y), ref2, bound2, 1e-13, "Hamiltonian alpha/beta")
 
 
-@pytest.mark.parametrize("plan", [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 256),
-                                  (5, 4096), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 2)])
+@pytest.mark.parametrize("plan", [(6, 7), (6, 9), (0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15),
+                                  (5, 256), (5, 4096), (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 2)])
 def test_hamiltonian_plans(ham, m_ham, plan):
     A, x, ref, bound = ham
     m_ham.set_plan(*plan)
@@ -148,14 +148,17 @@ def test_split_explicit_blocks_small():
     assert_within(host(y), ref, bound, 1e-13)
 
 
+@pytest.mark.parametrize("plan", [None, (6, 9), (6, 15)])
 @pytest.mark.parametrize("acc", ["ff", "f64"])
-def test_hamiltonian_fp32_storage(ham, acc):
+def test_hamiltonian_fp32_storage(ham, acc, plan):
     from paper_1106_5908_gb300 import Matrix
     A, x, _, _ = ham
     v32 = A.val.astype(np.float32)
     x32 = x.astype(np.float32)
     M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
     M.set_accumulator(acc)
+    if plan is not None:
+        M.set_plan(*plan)
     ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v32.astype(np.float64), x32.astype(np.float64),
                              with_bound=True)
     assert_within(host(M.apply(dev(x32))), ref, bound, 1e-6, f"Hamiltonian fp32 y32 {acc}")

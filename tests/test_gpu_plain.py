@@ -12,9 +12,9 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PLANS = [(0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 32), (5, 256), (5, 4096), (0, 16),
-         (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
-N_CHUNK_PLANS = 16  # plans before the row-vector kernel
+PLANS = [(6, 7), (6, 9), (0, 15), (0, 7), (3, 7), (3, 15), (4, 7), (4, 9), (4, 11), (4, 15), (5, 32), (5, 256), (5, 4096),
+         (0, 16), (0, 8), (2, 7), (2, 15), (2, 31), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16), (1, 32)]
+N_CHUNK_PLANS = 18  # plans before the row-vector kernel
 
 
 def make(A, dtype=None):
@@ -248,7 +248,7 @@ def test_fp32_widening_exact(acc, plan):
     assert np.array_equal(y[~nan], want[~nan]), np.flatnonzero(y[~nan] != want[~nan])[:8]
 
 
-@pytest.mark.parametrize("plan", [(5, 32), (5, 256), (5, 4096), (4, 9)])
+@pytest.mark.parametrize("plan", [(5, 32), (5, 256), (5, 4096), (4, 9), (6, 9), (6, 15)])
 @pytest.mark.parametrize("shape", [(300, 200), (20000, 20000)])
 def test_fp32_storage_plans(plan, shape):
     """FP32-stored values and vectors on the row-slice and slot-major kernels
@@ -268,7 +268,7 @@ def test_fp32_storage_plans(plan, shape):
         assert_within(host(y), ref, bound, 1e-6, f"fp32 {plan} a={alpha} b={beta}")
 
 
-@pytest.mark.parametrize("plan", [(4, 7), (4, 15), (5, 32), (5, 4096)])
+@pytest.mark.parametrize("plan", [(4, 7), (4, 15), (5, 32), (5, 4096), (6, 9)])
 def test_slot_major_follows_new_values(plan):
     """The slot-major copies (plan families 4 and 5) are laid out again after new
     values, in FP64 and in FP32 storage."""
