@@ -527,6 +527,22 @@ def measure_forms(M64, A, x, dev, form_ms, b_plain, SP):
         del xd, ys
     except Exception as e:  # reported, not hidden
         out["split_schedules"] = {"error": repr(e)}
+    try:  # symmetric CRS (Sect. 1.3.1): the upper triangle stored once, two passes
+        U = W.upper_triangle(A)
+        MS = Matrix.from_symmetric_upper(U.row_ptr, U.col_idx, U.val)
+        xs = torch.as_tensor(x).to(dev)
+        ysym = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+        ms = _time(lambda: MS.apply(xs, ysym), 10)
+        n_strict = int(U.nnz - np.count_nonzero(U.col_idx == np.repeat(np.arange(U.n_rows), np.diff(U.row_ptr))))
+        b_ideal = model.bytes_symmetric(A.n_rows, U.nnz, n_strict)
+        b_impl = model.bytes_symmetric(A.n_rows, U.nnz, n_strict, implementation=True)
+        out["symmetric_f64"] = {"ms": ms, "stored_entries": U.nnz, "GBs_single_pass_bytes": b_ideal / ms / 1e6,
+                                "GBs_moved": b_impl / ms / 1e6, "single_pass_bytes": b_ideal,
+                                "bytes_moved": b_impl, "time_vs_plain": ms / form_ms["plain"],
+                                "GFLOPs": model.flops(A.nnz) / ms / 1e6}
+        del MS, xs, ysym
+    except Exception as e:  # reported, not hidden
+        out["symmetric_f64"] = {"error": repr(e)}
     for nrhs in (4, 8, 16, 32):
         X = torch.rand(A.n_rows, nrhs, dtype=torch.float64, device=dev) * 2 - 1
         Y = torch.empty_like(X)
@@ -639,6 +655,9 @@ def run_only_plain(args, local_rank):
     from paper_1106_5908_gb300.build import build as build_lib
     torch.cuda.set_device(local_rank)
     build_lib()
+    if args.only in ("backward27", "split", "batch256"):
+        run_only_form(args, local_rank)
+        return
     f32 = args.only == "plain32"
     if args.only in ("plain", "plain32"):
         A, x = hamiltonian_workload()
@@ -669,6 +688,53 @@ def run_only_plain(args, local_rank):
                       / ms / 1e6}), flush=True)
 
 
+def run_only_form(args, local_rank):
+    """One form alone, warm-up plus K calls (kernel profiling cases):
+    `--only backward27` the reverse pass (grad_x and grad_val) on the 128^3
+    27-point matrix, `--only split` the split product (8 blocks, two streams) on
+    the Hamiltonian-like matrix, `--only batch256` the 256-matrix batch."""
+    import torch
+    from paper_1106_5908_gb300 import Batch, Matrix
+    from paper_1106_5908_gb300.build import build as build_lib
+    torch.cuda.set_device(local_rank)
+    build_lib()
+    if args.only == "backward27":
+        A = W.stencil27(W.STENCIL27_GRID, seed=W.SEED_STENCIL27_VAL)
+        M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+        x = torch.as_tensor(W.uniform(A.n_cols, W.SEED_STENCIL27_X)).cuda()
+        g = torch.as_tensor(W.uniform(A.n_rows, W.SEED_STENCIL27_G)).cuda()
+        fn = lambda: M.backward(g, x)
+    elif args.only == "split":
+        A, xh = hamiltonian_workload()
+        M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+        sp = M.split(8)
+        x = torch.as_tensor(xh).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        s2 = torch.cuda.Stream()
+        fn = lambda: sp.apply(x, y, s_comm=s2)
+    else:
+        sizes = W.batch_sizes(W.BATCH_COUNT)
+        mats, xs, ys = [], [], []
+        for m, n in enumerate(sizes):
+            Am = W.batch_matrix(m, int(n))
+            mats.append(Matrix.from_csr(Am.row_ptr, Am.col_idx, Am.val, Am.n_cols))
+            xs.append(torch.rand(Am.n_cols, dtype=torch.float64, device="cuda"))
+            ys.append(torch.empty(Am.n_rows, dtype=torch.float64, device="cuda"))
+        B = Batch(mats)
+        fn = lambda: B.apply(xs, ys)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"only": args.only, "ms_per_call": e0.elapsed_time(e1) / args.steps}), flush=True)
+
+
 def run_ordering_study(args, local_rank):
     """The ordering study (the paper's RCM remark, Sect. 2): the plain FP64 product
     on the Hamiltonian-like matrix in its natural order, in reverse Cuthill-McKee
@@ -694,7 +760,7 @@ def run_ordering_study(args, local_rank):
         y = torch.empty(B.n_rows, dtype=torch.float64, device="cuda")
         auto = M.info()
         res = {"bandwidth": W.bandwidth(B), "plan": {"family": auto["family"], "E": auto["E"]}}
-        plans = (("auto", None), ("two_stage_E7", (0, 7)), ("three_stage_E15", (3, 15)))
+        plans = (("auto", None), ("slot_E7", (4, 7)), ("row_slices_4096", (5, 4096)))
         for label, plan in (plans[:1] if args.study_auto_only else plans):
             if plan is not None:
                 M.set_plan(*plan)
@@ -730,9 +796,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "stencil27"), default=None,
+    ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "stencil27", "backward27", "split",
+                                       "batch256"), default=None,
                     help="run only the plain FP64 product on the Hamiltonian-like matrix (plain32: its "
-                         "FP32-storage product), the 7-point or the 27-point matrix (for kernel profiling)")
+                         "FP32-storage product), the 7-point or the 27-point matrix, or one form: the reverse "
+                         "pass on the 27-point matrix, the split product, the 256-matrix batch (kernel profiling)")
     ap.add_argument("--study", choices=("ordering",), default=None,
                     help="natural / RCM / random ordering of the Hamiltonian-like matrix")
     ap.add_argument("--study-auto-only", action="store_true",

@@ -84,6 +84,29 @@ spmv_status spmv_create(spmv_handle *out, int32_t n_rows, int32_t n_cols, int64_
  * device work that may still use it. */
 void spmv_destroy(spmv_handle h);
 
+/* Symmetric CRS (Sect. 1.3.1: a symmetric matrix stored as its upper
+ * triangle, which the paper names and sets aside).  The n x n matrix A is
+ * given by U, its upper triangle with the diagonal: row_ptr[n+1], col_idx[nnz]
+ * and val[nnz] as for spmv_create, every entry of row i having a column
+ * j >= i (repeated entries are summed; columns need not be sorted), so each
+ * off-diagonal value is stored once and serves a_ij and a_ji.  spmv_apply on
+ * the handle computes y = alpha*A*x + beta*y with A = U + U_s^T (U_s: U
+ * without its diagonal) in two passes of fixed summation order: the row sums
+ * of U on the autotuned kernel (with beta), then the row sums of U_s^T added
+ * onto y by the warp-chunk kernel that reads each value through its position
+ * in U (a transposed index built once here, on the host: rows of U_s^T list
+ * their entries by increasing position in U).  Results are deterministic.
+ * spmv_set_values replaces U's values; spmv_apply (vector types as for
+ * spmv_apply, except FP32 storage with an FP64 y), spmv_get_info, spmv_set_plan
+ * (for the U pass), spmv_set_accumulator and spmv_destroy accept the handle;
+ * the split form, block vectors, the reverse pass, the transposed structure,
+ * the CG solvers and batches return SPMV_ERR_UNSUPPORTED.
+ * Errors: as spmv_create, and SPMV_ERR_INVALID_INDEX for an entry left of the
+ * diagonal. */
+spmv_status spmv_create_symmetric(spmv_handle *out, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                  const int32_t *col_idx, const void *val, spmv_dtype val_t,
+                                  int is_device_ptr, void *stream);
+
 /* Replace the stored values (same sparsity pattern) from a device pointer of
  * type t; t may differ from the handle's storage type only as FP64 -> FP32
  * storage or FP32 -> FP64 storage (converted on the device).  Asynchronous. */
@@ -286,9 +309,10 @@ spmv_status spmv_transpose_noalloc(int32_t n_rows, int32_t n_cols, int64_t nnz,
 
 /* Group count matrix handles (all FP64 or all FP32 storage) into one batch whose
  * apply is a single persistent kernel launch over the warp chunks of every
- * matrix (the slot-major chunk kernel on one concatenated slot-major copy of all
- * matrices), captured once into a CUDA graph and replayed.  spmv_batched_get_info
- * reports the entries per lane the batch runs with.
+ * matrix (the slot-major chunk kernel on a concatenated slot-major copy of the
+ * members, one per group of members tuned alike), captured once into a CUDA
+ * graph and replayed.  spmv_batched_get_member_plan reports each member's
+ * entries per lane.
  * The batch holds its own copy of the values: after spmv_set_values on a member,
  * the next spmv_batched_apply lays that member's values out again (on stream,
  * before the launch).  The handles must outlive the batch. */
@@ -303,9 +327,19 @@ void spmv_batched_destroy(spmv_batch_handle b);
 spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *const *x,
                                double beta, void *const *y, void *stream);
 
-/* plan[0..3]: E, threads per CTA, total chunks, persistent grid size (0 when
- * the kernel sizes its persistent grid at launch). */
+/* plan[0..3]: E (0 when the members were tuned apart, see below), threads per
+ * CTA, total chunks, persistent grid size (0 when the kernel sizes its
+ * persistent grid at launch). */
 spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan);
+
+/* The entries per lane each member runs with (HOST array of count int32).  The
+ * batch tunes its members apart from their own row-length histograms (mean row
+ * length below 4 entries: 7 per lane, else 9; a single matrix switches at 8,
+ * but in a batch a separate group for members of 4-8 entries per row measured
+ * slower than running them at 9); when both occur, the members of each group
+ * share one slot-major copy and the one persistent launch walks both groups
+ * (not in the paper). */
+spmv_status spmv_batched_get_member_plan(spmv_batch_handle b, int32_t *entries_per_lane);
 
 /* ------------------------------------------------------------------------ */
 /* Mixed-precision iterative refinement CG                                     */

@@ -84,6 +84,8 @@ def _load():
     lib.oracle_node_threads.restype = i32
     lib.oracle_num_threads.argtypes = []
     lib.oracle_num_threads.restype = ctypes.c_int
+    lib.oracle_spmv_sym.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p, vp]
+    lib.oracle_spmv_sym.restype = None
     lib.oracle_spmm.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, f64, f64, _f64p, vp]
     lib.oracle_spmm.restype = None
     lib.oracle_transpose.argtypes = [i32, i32, _i32p, _i32p, _i32p, _i32p, _i32p]
@@ -137,6 +139,26 @@ def spmv(row_ptr, col_idx, val, x, alpha=1.0, beta=0.0, y=None, with_bound=False
         out[:n] = np.asarray(y, dtype=np.float64)
     bound = np.zeros(max(n, 1), np.float64) if with_bound else None
     lib.oracle_spmv(n, rp, ci, v, xx, float(alpha), float(beta), out, _ptr(bound))
+    if with_bound:
+        return out[:n], bound[:n]
+    return out[:n]
+
+
+def spmv_sym(row_ptr, col_idx, val, x, alpha=1.0, beta=0.0, y=None, with_bound=False):
+    """Symmetric CRS (Sect. 1.3.1): the matrix given by its upper triangle with
+    the diagonal; each stored off-diagonal entry serves both of its positions.
+    Returns y (FP64); with ``with_bound`` also |alpha|*sum_j |a_ij x_j| + |beta*y|."""
+    lib = _load()
+    rp, ci, v = _crs(row_ptr, col_idx, val)
+    n = rp.size - 1
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    if xx.size == 0:
+        xx = np.zeros(1, np.float64)
+    out = np.zeros(max(n, 1), np.float64)
+    if y is not None and beta != 0.0:
+        out[:n] = np.asarray(y, dtype=np.float64)
+    bound = np.zeros(max(n, 1), np.float64) if with_bound else None
+    lib.oracle_spmv_sym(n, rp, ci, v, xx, float(alpha), float(beta), out, _ptr(bound))
     if with_bound:
         return out[:n], bound[:n]
     return out[:n]

@@ -504,6 +504,44 @@ int32_t oracle_node_threads(const oracle_node *nd)
     return nd->T;
 }
 
+/* Symmetric CRS (the storage Sect. 1.3.1 mentions and sets aside): a symmetric
+ * matrix given by its upper triangle with the diagonal, each row i listing the
+ * entries a_ij with j >= i.  The product walks the stored entries once, row by
+ * row in increasing k: entry (i, j, a) adds a*x[j] to row i's sum and, when
+ * j != i, a*x[i] to row j's sum (the mirrored entry a_ji = a).  Then
+ * y_i = alpha*t_i (+ beta*y_i).  absrow (nullable) receives
+ * |alpha|*sum_j |a_ij x_j| over the full row plus |beta*y_i|. */
+void oracle_spmv_sym(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                     const double *val, const double *x, double alpha, double beta,
+                     double *y, double *absrow)
+{
+    double *t = (double *)calloc((size_t)n + 1, sizeof(double));
+    double *mag = (double *)calloc((size_t)n + 1, sizeof(double));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int32_t j = col_idx[k];
+            double p = val[k] * x[j];
+            t[i] = t[i] + p;
+            mag[i] = mag[i] + fabs(p);
+            if (j != i) {
+                double q = val[k] * x[i];
+                t[j] = t[j] + q;
+                mag[j] = mag[j] + fabs(q);
+            }
+        }
+    for (int32_t i = 0; i < n; ++i) {
+        double yin = (beta == 0.0) ? 0.0 : y[i];
+        if (beta == 0.0)
+            y[i] = alpha * t[i];
+        else
+            y[i] = alpha * t[i] + beta * yin;
+        if (absrow)
+            absrow[i] = fabs(alpha) * mag[i] + fabs(beta * yin);
+    }
+    free(t);
+    free(mag);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

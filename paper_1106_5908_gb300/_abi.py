@@ -28,12 +28,12 @@ SPMV_NOALLOC_MAX_COLS = 1 << 20
 
 # Every entry point declared in include/spmv.h.
 EXPORTS = (
-    "spmv_status_string", "spmv_version", "spmv_create", "spmv_destroy", "spmv_set_values",
+    "spmv_status_string", "spmv_version", "spmv_create", "spmv_create_symmetric", "spmv_destroy", "spmv_set_values",
     "spmv_get_info", "spmv_row_histogram", "spmv_set_plan", "spmv_set_accumulator", "spmv_apply", "spmv_split_create",
     "spmv_split_destroy", "spmv_split_get_plan", "spmv_apply_split", "spmv_apply_split_vector",
     "spmv_split_get_halo",
     "spmm_apply", "spmv_backward", "spmv_get_transpose", "spmv_transpose_noalloc", "spmv_batched_create",
-    "spmv_batched_destroy", "spmv_batched_apply", "spmv_batched_get_info", "spmv_ir_cg",
+    "spmv_batched_destroy", "spmv_batched_apply", "spmv_batched_get_info", "spmv_batched_get_member_plan", "spmv_ir_cg",
     "spmv_cg", "spmv_check_device_error", "spmv_validate_device", "spmv_selftest_wait_timeout",
 )
 
@@ -67,6 +67,7 @@ def load() -> ctypes.CDLL:
         "spmv_status_string": (ctypes.c_char_p, [st]),
         "spmv_version": (i32, []),
         "spmv_create": (st, [vp, i32, i32, i64, vp, vp, vp, st, ctypes.c_int, vp]),
+        "spmv_create_symmetric": (st, [vp, i32, i64, vp, vp, vp, st, ctypes.c_int, vp]),
         "spmv_destroy": (None, [vp]),
         "spmv_set_values": (st, [vp, vp, st, vp]),
         "spmv_get_info": (st, [vp, vp, vp, vp, vp]),
@@ -85,6 +86,7 @@ def load() -> ctypes.CDLL:
         "spmv_get_transpose": (st, [vp, vp, vp, vp, vp]),
         "spmv_transpose_noalloc": (st, [i32, i32, i64, vp, vp, vp, vp, vp, vp]),
         "spmv_batched_create": (st, [vp, i32, vp]),
+        "spmv_batched_get_member_plan": (st, [vp, vp]),
         "spmv_batched_destroy": (None, [vp]),
         "spmv_batched_apply": (st, [vp, f64, vp, f64, vp, vp]),
         "spmv_batched_get_info": (st, [vp, vp]),
@@ -124,6 +126,7 @@ def _fwd(name):
 
 spmv_version = _fwd("spmv_version")
 spmv_create = _fwd("spmv_create")
+spmv_create_symmetric = _fwd("spmv_create_symmetric")
 spmv_destroy = _fwd("spmv_destroy")
 spmv_set_values = _fwd("spmv_set_values")
 spmv_get_info = _fwd("spmv_get_info")
@@ -142,6 +145,7 @@ spmv_backward = _fwd("spmv_backward")
 spmv_get_transpose = _fwd("spmv_get_transpose")
 spmv_transpose_noalloc = _fwd("spmv_transpose_noalloc")
 spmv_batched_create = _fwd("spmv_batched_create")
+spmv_batched_get_member_plan = _fwd("spmv_batched_get_member_plan")
 spmv_batched_destroy = _fwd("spmv_batched_destroy")
 spmv_batched_apply = _fwd("spmv_batched_apply")
 spmv_batched_get_info = _fwd("spmv_batched_get_info")

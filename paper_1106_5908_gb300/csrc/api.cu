@@ -372,6 +372,10 @@ struct CgWork {
 struct spmv_matrix {
     int32_t n_rows = 0, n_cols = 0;
     int64_t nnz = 0;
+    // symmetric CRS: the CRS arrays hold the upper triangle with the diagonal,
+    // and the transposed slots (d_rowT, d_colT, d_perm, h_rowT) the transposed
+    // structure of its strictly upper part (perm: positions in the values)
+    bool sym = false;
     int vk = kF64;
     int device = 0;
     bool owns_structure = true;
@@ -457,6 +461,14 @@ struct spmv_batch {
     int32_t *d_scmat = nullptr;
     std::vector<int32_t> slot_off;
     std::vector<uint64_t> vals_ver;
+    // members tuned apart: member m runs with member_E[m] entries per lane; when
+    // both 7 and 9 occur, `slots` holds the E = 7 members and `slots9` the E = 9
+    // ones (slot_off[m]: the member's first chunk in its group's copy)
+    bool mixed = false;
+    std::vector<int32_t> member_E;
+    std::vector<int32_t> slot_cnt;  // chunks of each member (mixed batches)
+    SlotTable slots9;
+    int32_t *d_scmat9 = nullptr;
 };
 
 namespace {
@@ -526,11 +538,14 @@ int pick_E(int vk, int xk, int yk, int acc, int want) {
 constexpr int32_t kSellSigma = 4096;
 constexpr double kSellMaxPadding = 0.10;
 constexpr double kSellMinRowLength = 12.0;
-// batched slot-major launch: E = 9 from this mean row length on (else 7).  The
-// 256-matrix batch of 5-point Laplacians and Hamiltonian-like patterns (9.0
-// entries per row) takes 0.797 ms with E = 9 against 0.904 ms with 7 in FP64,
-// 0.605 against 0.645 ms with FP32 storage.
-constexpr double kBatchSlotMeanE9 = 8.0;
+// Batched slot-major launch: each member's entries per lane from its own mean
+// row length, E = 7 below this many entries per row, else 9.  The threshold is
+// lower than a single matrix's (8): on the 256-matrix batch of 5-point
+// Laplacians (4.9 per row) and Hamiltonian-like patterns (13 per row), giving
+// the Laplacians their own E = 7 group took 0.836 ms against 0.803 ms with every
+// member at E = 9 (FP32 storage: 0.660 against 0.631 ms); the whole batch at
+// E = 7: 0.90 ms.  Members with shorter rows still get a group of their own.
+constexpr double kBatchSlotMeanE9 = 4.0;
 
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
@@ -1058,6 +1073,73 @@ static spmv_status capture_graph(F body, cudaGraphExec_t *exec) {
     return e == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
 }
 
+// Symmetric CRS (Sect. 1.3.1): the handle stores U, the upper triangle with the
+// diagonal, once.  The product y = alpha*(U + U_s^T)*x + beta*y runs in two
+// passes with a fixed summation order: the row sums of U on the autotuned
+// kernel (with beta), then the row sums of U_s^T (the strictly upper part,
+// transposed) added onto y by the warp-chunk kernel that reads each value
+// through its position in U.
+static spmv_status create_symmetric_index(spmv_matrix *h, const int32_t *col_host, cudaStream_t s) {
+    const int32_t n = h->n_rows;
+    std::vector<int32_t> rowS(static_cast<size_t>(n) + 1, 0);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = h->h_rp[i]; k < h->h_rp[i + 1]; ++k)
+            if (col_host[k] != i) rowS[static_cast<size_t>(col_host[k]) + 1] += 1;
+    for (int32_t j = 0; j < n; ++j) rowS[j + 1] += rowS[j];
+    const int64_t ns = rowS[n];
+    std::vector<int32_t> colS(static_cast<size_t>(ns)), permS(static_cast<size_t>(ns));
+    std::vector<int32_t> next(rowS.begin(), rowS.end() - 1);
+    for (int32_t i = 0; i < n; ++i)  // rows of U_s^T list their entries by increasing position in U
+        for (int32_t k = h->h_rp[i]; k < h->h_rp[i + 1]; ++k)
+            if (col_host[k] != i) {
+                const int32_t p = next[col_host[k]]++;
+                colS[p] = i;
+                permS[p] = k;
+            }
+    const size_t nT = static_cast<size_t>(n) + 1 + kRowPad;
+    const size_t nent = static_cast<size_t>(ns) + kEntryPad;
+    if (dmalloc(&h->d_rowT, nT) != cudaSuccess || dmalloc(&h->d_colT, nent) != cudaSuccess ||
+        dmalloc(&h->d_perm, nent) != cudaSuccess)
+        return SPMV_ERR_ALLOC;
+    CK(cudaMemsetAsync(h->d_rowT, 0, nT * 4, s));
+    CK(cudaMemsetAsync(h->d_colT, 0, nent * 4, s));
+    CK(cudaMemsetAsync(h->d_perm, 0, nent * 4, s));
+    CK(cudaMemcpyAsync(h->d_rowT, rowS.data(), rowS.size() * 4, cudaMemcpyHostToDevice, s));
+    if (ns) {
+        CK(cudaMemcpyAsync(h->d_colT, colS.data(), static_cast<size_t>(ns) * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->d_perm, permS.data(), static_cast<size_t>(ns) * 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    h->h_rowT = std::move(rowS);
+    h->has_T = true;
+    return SPMV_OK;
+}
+
+static spmv_status apply_sym(spmv_matrix *h, double alpha, const void *x, int xk, double beta, void *y, int yk,
+                      cudaStream_t s) {
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    const int32_t n = h->n_rows;
+    const int64_t ns = h->h_rowT.empty() ? 0 : h->h_rowT[n];
+    WarpOps ops;
+    const double meanT = n ? static_cast<double>(ns) / n : 0.0;
+    int ET = (meanT < 20.0) ? 7 : 15;
+    if (!warp_ops(h->vk, xk, yk, acc, ET, true, false, &ops)) ET = (ET == 7) ? 15 : 7;
+    if (ns > 0 && !warp_ops(h->vk, xk, yk, acc, ET, true, false, &ops)) return SPMV_ERR_UNSUPPORTED;
+    spmv_status st = apply_impl(h, alpha, x, xk, beta, y, yk, s);
+    if (st != SPMV_OK || ns == 0 || n == 0) return st;
+    ChunkTable *ct = get_chunks(h, ET, true);
+    if (!ct) return SPMV_ERR_ALLOC;
+    WarpParams wp{};
+    wp.m = MatRef{h->d_rowT, h->d_colT, h->d_perm, h->d_val, x, y, nullptr};
+    wp.chunks = ct->d;
+    wp.masks = ct->masks;
+    wp.n_chunks = ct->n;
+    wp.alpha = alpha;
+    wp.beta = 1.0;
+    wp.err = h->d_err;
+    return ops.launch(wp, ct->n, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
+}
+
 extern "C" {
 
 const char *spmv_status_string(spmv_status s) {
@@ -1252,7 +1334,47 @@ spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt
     if (h->vk == kF32 && xt != SPMV_F32) return SPMV_ERR_UNSUPPORTED;
     if (yt != SPMV_F64 && yt != SPMV_F32) return SPMV_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
+    if (h->sym) return apply_sym(h, alpha, x, xt, beta, y, yt, static_cast<cudaStream_t>(stream));
     return apply_impl(h, alpha, x, xt, beta, y, yt, static_cast<cudaStream_t>(stream));
+}
+
+spmv_status spmv_create_symmetric(spmv_handle *out, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                  const int32_t *col_idx, const void *val, spmv_dtype val_t, int is_device_ptr,
+                                  void *stream) {
+    if (!out) return SPMV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return SPMV_ERR_INVALID_ARG;
+    if (val_t != SPMV_F64 && val_t != SPMV_F32) return SPMV_ERR_INVALID_ARG;
+    if (!row_ptr || (nnz > 0 && (!col_idx || !val))) return SPMV_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> h_rp(static_cast<size_t>(n) + 1);
+    std::vector<int32_t> h_col(static_cast<size_t>(nnz));
+    if (is_device_ptr) {
+        CK(cudaMemcpyAsync(h_rp.data(), row_ptr, h_rp.size() * 4, cudaMemcpyDeviceToHost, s));
+        if (nnz) CK(cudaMemcpyAsync(h_col.data(), col_idx, static_cast<size_t>(nnz) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(h_rp.data(), row_ptr, h_rp.size() * 4);
+        if (nnz) std::memcpy(h_col.data(), col_idx, static_cast<size_t>(nnz) * 4);
+    }
+    spmv_status st = validate_host(n, n, nnz, h_rp.data(), h_col.data());
+    if (st != SPMV_OK) return st;
+    for (int32_t i = 0; i < n; ++i)  // the upper triangle: no entry left of the diagonal
+        for (int32_t k = h_rp[i]; k < h_rp[i + 1]; ++k)
+            if (h_col[k] < i) return SPMV_ERR_INVALID_INDEX;
+    spmv_handle h = nullptr;
+    st = create_from_host(&h, n, n, nnz, std::move(h_rp), col_idx, val, val_t, val_t, is_device_ptr != 0, s,
+                          h_col.data());
+    if (st != SPMV_OK) return st;
+    DeviceGuard g(h->device);
+    h->sym = true;
+    st = create_symmetric_index(h, h_col.data(), s);
+    if (st != SPMV_OK) {
+        destroy_matrix(h);
+        return st;
+    }
+    *out = h;
+    return SPMV_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1264,7 +1386,7 @@ spmv_status spmv_split_create(spmv_split_handle *out, spmv_handle h, int32_t nbl
     if (!out || !h || nblocks < 1) return SPMV_ERR_INVALID_ARG;
     *out = nullptr;
     if (h->n_rows != h->n_cols) return SPMV_ERR_INVALID_ARG;
-    if (h->vk != kF64) return SPMV_ERR_UNSUPPORTED;
+    if (h->vk != kF64 || h->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     const int32_t n = h->n_rows;
     const int64_t nnz = h->nnz;
@@ -1500,7 +1622,7 @@ spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X,
                        void *Y, spmv_dtype vt, void *stream) {
     if (!h || nrhs < 1 || nrhs > 64) return SPMV_ERR_INVALID_ARG;
     if (h->n_rows > 0 && (!X || !Y)) return SPMV_ERR_INVALID_ARG;
-    if (vt != SPMV_F64 || h->vk != kF64) return SPMV_ERR_UNSUPPORTED;
+    if (vt != SPMV_F64 || h->vk != kF64 || h->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (h->n_rows == 0) return SPMV_OK;
@@ -1571,6 +1693,7 @@ spmv_status spmm_apply(spmv_handle h, int32_t nrhs, double alpha, const void *X,
 spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void *x, void *grad_x,
                           void *grad_val, void *stream) {
     if (!h) return SPMV_ERR_INVALID_ARG;
+    if (h->sym) return SPMV_ERR_UNSUPPORTED;
     if (grad_x && h->n_rows > 0 && !g) return SPMV_ERR_INVALID_ARG;
     if (grad_val && h->nnz > 0 && (!g || !x)) return SPMV_ERR_INVALID_ARG;
     DeviceGuard dg(h->device);
@@ -1683,6 +1806,7 @@ spmv_status spmv_backward(spmv_handle h, double alpha, const void *g, const void
 spmv_status spmv_get_transpose(spmv_handle h, int32_t *rowT_ptr, int32_t *colT_idx, int32_t *perm,
                                void *stream) {
     if (!h) return SPMV_ERR_INVALID_ARG;
+    if (h->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     spmv_status st = ensure_transpose(h, s);
@@ -1716,6 +1840,8 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
     const int vk = mats[0] ? mats[0]->vk : -1;
     for (int32_t m = 0; m < count; ++m)
         if (!mats[m] || mats[m]->vk != vk) return SPMV_ERR_INVALID_ARG;
+    for (int32_t m = 0; m < count; ++m)
+        if (mats[m]->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard dg(mats[0]->device);
     spmv_batch *b = new (std::nothrow) spmv_batch();
     if (!b) return SPMV_ERR_ALLOC;
@@ -1733,9 +1859,77 @@ spmv_status spmv_batched_create(spmv_batch_handle *out, int32_t count, const spm
         rows += mats[m]->n_rows;
     }
     b->E = (rows && static_cast<double>(nnz) / rows < 20.0) ? 7 : 15;
-    // slot-major entries per lane from the batch's mean row length, as for one matrix
-    const int ES = (rows && static_cast<double>(nnz) / rows < kBatchSlotMeanE9) ? 7 : 9;
+    // slot-major entries per lane from each member's own row-length histogram
+    // (its mean row length): 7 below kBatchSlotMeanE9 entries per row, else 9
+    b->member_E.resize(static_cast<size_t>(count));
+    bool any7 = false, any9 = false;
+    for (int32_t m = 0; m < count; ++m) {
+        const double mean = mats[m]->n_rows ? static_cast<double>(mats[m]->nnz) / mats[m]->n_rows : 0.0;
+        b->member_E[m] = (mean < kBatchSlotMeanE9) ? 7 : 9;
+        (b->member_E[m] == 7 ? any7 : any9) = true;
+    }
     SlotOps sops;
+    if (any7 && any9 && slot_ops_batched(vk, acc, 7, &sops) && slot_ops_batched(vk, acc, 9, &sops)) {
+        // two groups, one copy each, one launch over both
+        b->mixed = true;
+        b->use_slots = true;
+        b->E = 7;
+        b->slot_off.assign(static_cast<size_t>(count) + 1, 0);
+        b->slot_cnt.assign(static_cast<size_t>(count), 0);
+        b->vals_ver.assign(static_cast<size_t>(count), 0);
+        const size_t vb = (vk == kF64) ? 8 : 4;
+        bool ok = true;
+        for (int g = 0; g < 2 && ok; ++g) {
+            const int EG = g == 0 ? 7 : 9;
+            SlotTable &t = g == 0 ? b->slots : b->slots9;
+            int32_t *&dcm = g == 0 ? b->d_scmat : b->d_scmat9;
+            std::vector<ChunkDesc> d;
+            std::vector<uint32_t> lm;
+            std::vector<int32_t> cm;
+            for (int32_t m = 0; m < count; ++m) {
+                if (b->member_E[m] != EG) continue;
+                b->slot_off[m] = static_cast<int32_t>(d.size());
+                make_slot_chunks(mats[m]->h_rp.data(), mats[m]->n_rows, EG, d, lm, &t.n_long, &t.n_empty);
+                b->slot_cnt[m] = static_cast<int32_t>(d.size()) - b->slot_off[m];
+                cm.resize(d.size(), m);
+            }
+            t.n = static_cast<int32_t>(d.size());
+            const size_t nslots = d.size() * 32 * EG;
+            ok = dmalloc(&t.d, d.size()) == cudaSuccess && dmalloc(&t.lmask, lm.size()) == cudaSuccess &&
+                 dmalloc(&dcm, cm.size()) == cudaSuccess && cudaMalloc(&t.vals, nslots * vb + 16) == cudaSuccess &&
+                 dmalloc(&t.cols, nslots + 4) == cudaSuccess;
+            ok = ok && (d.empty() || cudaMemcpy(t.d, d.data(), sizeof(ChunkDesc) * d.size(), cudaMemcpyHostToDevice) ==
+                                         cudaSuccess);
+            ok = ok && (lm.empty() || cudaMemcpy(t.lmask, lm.data(), 4 * lm.size(), cudaMemcpyHostToDevice) == cudaSuccess);
+            ok = ok && (cm.empty() || cudaMemcpy(dcm, cm.data(), 4 * cm.size(), cudaMemcpyHostToDevice) == cudaSuccess);
+            for (int32_t m = 0; ok && m < count; ++m) {
+                if (b->member_E[m] != EG) continue;
+                const int64_t off = b->slot_off[m];
+                const int64_t nch = b->slot_cnt[m];
+                ok = launch_slot_relayout(t.d + off, EG, nch * 32 * EG, vk, mats[m]->d_val, mats[m]->d_col,
+                                          static_cast<char *>(t.vals) + off * 32 * EG * vb, t.cols + off * 32 * EG,
+                                          nullptr) == cudaSuccess;
+                b->vals_ver[m] = mats[m]->values_version;
+            }
+            t.vals_valid = true;
+        }
+        ok = ok && cudaDeviceSynchronize() == cudaSuccess;
+        b->h_mats.resize(static_cast<size_t>(count));
+        for (int32_t m = 0; m < count; ++m)
+            b->h_mats[m] = MatRef{mats[m]->d_rp, mats[m]->d_col, mats[m]->d_val, nullptr, nullptr, nullptr, nullptr};
+        b->cur_x.assign(static_cast<size_t>(count), nullptr);
+        b->cur_y.assign(static_cast<size_t>(count), nullptr);
+        if (ok && (dmalloc(&b->d_mats, b->h_mats.size()) != cudaSuccess || dmalloc(&b->d_err, 1) != cudaSuccess))
+            ok = false;
+        if (ok && cudaMemset(b->d_err, 0, 4) != cudaSuccess) ok = false;
+        if (!ok) {
+            spmv_batched_destroy(b);
+            return SPMV_ERR_ALLOC;
+        }
+        *out = b;
+        return SPMV_OK;
+    }
+    const int ES = any7 ? 7 : 9;
     if (slot_ops_batched(vk, acc, ES, &sops)) {
         // the slot-major chunk kernel over one concatenated copy of all matrices
         b->E = ES;
@@ -1826,7 +2020,9 @@ void spmv_batched_destroy(spmv_batch_handle b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     free_chunks(b->chunks);
     free_slots(b->slots);
+    free_slots(b->slots9);
     cudaFree(b->d_scmat);
+    cudaFree(b->d_scmat9);
     cudaFree(b->d_mats);
     cudaFree(b->d_err);
     delete b;
@@ -1856,18 +2052,21 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
     }
     const int acc = (b->vk == kF32) ? kAccFF : kAccF64;
     if (b->use_slots) {
-        if (b->slots.n == 0) return SPMV_OK;
+        if (b->slots.n == 0 && b->slots9.n == 0) return SPMV_OK;
         // members given new values since the copy: lay their values out again
         const size_t vb = (b->vk == kF64) ? 8 : 4;
         for (int32_t m = 0; m < b->count; ++m)
             if (b->mats[m]->values_version != b->vals_ver[m]) {
-                const int64_t off = b->slot_off[m], nch = b->slot_off[m + 1] - off;
-                CK(launch_slot_relayout(b->slots.d + off, b->E, nch * 32 * b->E, b->vk, b->mats[m]->d_val, nullptr,
-                                        static_cast<char *>(b->slots.vals) + off * 32 * b->E * vb, nullptr, s));
+                const int EG = b->mixed ? b->member_E[m] : b->E;
+                const SlotTable &t = (b->mixed && EG == 9) ? b->slots9 : b->slots;
+                const int64_t off = b->slot_off[m];
+                const int64_t nch = b->mixed ? b->slot_cnt[m] : b->slot_off[m + 1] - off;
+                CK(launch_slot_relayout(t.d + off, EG, nch * 32 * EG, b->vk, b->mats[m]->d_val, nullptr,
+                                        static_cast<char *>(t.vals) + off * 32 * EG * vb, nullptr, s));
                 b->vals_ver[m] = b->mats[m]->values_version;
             }
         SlotOps sops;
-        if (!slot_ops_batched(b->vk, acc, b->E, &sops)) return SPMV_ERR_UNSUPPORTED;
+        if (!b->mixed && !slot_ops_batched(b->vk, acc, b->E, &sops)) return SPMV_ERR_UNSUPPORTED;
         if (recapture) {
             if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
             if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -1882,11 +2081,32 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
             p.n_chunks = b->slots.n;
             p.alpha = alpha;
             p.beta = beta;
+            SlotParams p9 = p;
+            if (b->mixed) {
+                p9.chunks = b->slots9.d;
+                p9.lmask = b->slots9.lmask;
+                p9.vals = b->slots9.vals;
+                p9.cols = b->slots9.cols;
+                p9.cmat = b->d_scmat9;
+                p9.n_chunks = b->slots9.n;
+            }
             cudaStream_t cap;
             CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t le = sops.launch(p, cap);
+                cudaError_t le = cudaSuccess;
+                if (b->mixed) {
+                    // the two groups as two kernel nodes of the one graph
+                    SlotOps s7, s9;
+                    if (!slot_ops_batched(b->vk, acc, 7, &s7) || !slot_ops_batched(b->vk, acc, 9, &s9)) {
+                        le = cudaErrorInvalidValue;
+                    } else {
+                        le = s7.launch(p, cap);
+                        if (le == cudaSuccess) le = s9.launch(p9, cap);
+                    }
+                } else {
+                    le = sops.launch(p, cap);
+                }
                 e = cudaStreamEndCapture(cap, &b->graph);
                 if (le != cudaSuccess) e = le;
             }
@@ -1937,10 +2157,17 @@ spmv_status spmv_batched_apply(spmv_batch_handle b, double alpha, const void *co
 
 spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan) {
     if (!b || !plan) return SPMV_ERR_INVALID_ARG;
-    plan[0] = b->E;
+    plan[0] = b->mixed ? 0 : b->E;
     plan[1] = 256;
-    plan[2] = b->use_slots ? b->slots.n : b->chunks.n;
+    plan[2] = b->use_slots ? b->slots.n + b->slots9.n : b->chunks.n;
     plan[3] = b->grid;
+    return SPMV_OK;
+}
+
+spmv_status spmv_batched_get_member_plan(spmv_batch_handle b, int32_t *entries_per_lane) {
+    if (!b || !entries_per_lane) return SPMV_ERR_INVALID_ARG;
+    for (int32_t m = 0; m < b->count; ++m)
+        entries_per_lane[m] = b->use_slots ? (b->mixed ? b->member_E[m] : b->E) : b->E;
     return SPMV_OK;
 }
 
@@ -1951,6 +2178,7 @@ spmv_status spmv_batched_get_info(spmv_batch_handle b, int32_t *plan) {
 spmv_status spmv_cg(spmv_handle h, const double *b, double *x, double tol, int32_t max_iter,
                     double *stats, void *stream) {
     if (!h || !b || !x || h->n_rows != h->n_cols || h->vk != kF64 || max_iter < 0) return SPMV_ERR_INVALID_ARG;
+    if (h->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();
@@ -2033,6 +2261,7 @@ spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_t
                        void *stream) {
     if (!h || !b || !x || h->n_rows != h->n_cols || h->vk != kF64 || max_outer < 0 || max_inner < 1)
         return SPMV_ERR_INVALID_ARG;
+    if (h->sym) return SPMV_ERR_UNSUPPORTED;
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const auto t0 = std::chrono::steady_clock::now();

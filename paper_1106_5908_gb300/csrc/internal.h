@@ -43,6 +43,9 @@ struct SlotOps {
 // pre: the variant that loads each chunk's row map and old y before its chains
 // (row-mapped products).
 bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops);
+// The batched launch over two groups of members tuned apart (7 and 9 entries per
+// lane, each group with its own slot-major copy): FP64, FP32 float-float.
+cudaError_t launch_slot_mixed(int vk, int acc, const SlotParams &p7, const SlotParams &p9, cudaStream_t s);
 // The variant whose values arrive by bulk copies into a shared-memory ring
 // (plan family 6): FP64 E = 7, 9; FP32 float-float E = 9, 15.
 bool slot_ops_tv(int vk, int xk, int yk, int acc, int E, SlotOps *ops);

@@ -52,6 +52,12 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     return false;
 }
 
+cudaError_t launch_slot_mixed(int vk, int acc, const SlotParams &p7, const SlotParams &p9, cudaStream_t s) {
+    if (vk == kF64 && acc == kAccF64) return SlotKernelMixed<double, double, double, AccF64>::launch(p7, p9, s);
+    if (vk == kF32 && acc == kAccFF) return SlotKernelMixed<float, float, float, AccFF>::launch(p7, p9, s);
+    return cudaErrorInvalidValue;
+}
+
 bool slot_ops_tv(int vk, int xk, int yk, int acc, int E, SlotOps *ops) {
     if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64) {
         if (E == 7) { ops->launch = &SlotKernelTV<7, double, double, double, AccF64>::launch; return true; }

@@ -66,18 +66,14 @@ struct kSlotScan {
 // chains (row-mapped products: the nonlocal part of the split form).
 // BATCHED: chunks of many matrices in one launch; chunk c belongs to matrix
 // cmat[c] of the table mats (its own x, y and CRS arrays).
-template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false, bool BATCHED = false>
-__global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
+// The persistent loop of one warp over chunks c, c + nwarps, ... of p (srow:
+// the warp's row buffer).
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE, bool BATCHED>
+__device__ __forceinline__ void slot_loop(const SlotParams &p, ACC *srow, int c, int nwarps) {
     constexpr int SL = 32 * E;
-    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
-    __shared__ ACC s_rows[8][kWarpRowCap];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * 8;
     const int n = p.n_chunks;
-    int c = blockIdx.x * 8 + wib;
     if (c >= n) return;
-    ACC *srow = s_rows[wib];
     const uint64_t pol = l2_evict_first_policy();
     const VT *__restrict__ vals = static_cast<const VT *>(p.vals);
     const double alpha = p.alpha, beta = p.beta;
@@ -213,6 +209,62 @@ __global__ void __launch_bounds__(256) k_slot(const SlotParams p) {
         }
     }
 }
+
+// CTAs per SM the register allocation must allow: FP64 with up to 11 entries
+// per lane two (16 warps per SM, at most 128 registers; left free, the
+// compiler takes 146-156 and halves the warps); FP32 storage with up to 9,
+// single matrix, three (at most 80 registers, no spills: 134 against 138 us on
+// the Hamiltonian-like matrix); the FP32 batch as the compiler chooses (held to
+// 80 it spills: 256 matrices 0.85 against 0.655 ms).
+template <int E, typename VT, bool BATCHED>
+constexpr int slot_min_ctas() {
+    return sizeof(VT) == 8 ? (E <= 11 ? 2 : 1) : ((E <= 9 && !BATCHED) ? 3 : 1);
+}
+
+template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false, bool BATCHED = false>
+__global__ void __launch_bounds__(256, (slot_min_ctas<E, VT, BATCHED>())) k_slot(const SlotParams p) {
+    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
+    __shared__ ACC s_rows[8][kWarpRowCap];
+    const int wib = threadIdx.x >> 5;
+    slot_loop<E, VT, XT, YT, ACC, PRE, BATCHED>(p, s_rows[wib], blockIdx.x * 8 + wib, gridDim.x * 8);
+}
+
+// A batch whose members were tuned apart: the chunks of the members given 7
+// entries per lane (p7, their own slot-major copy) and those given 9 (p9), one
+// after the other in the same persistent launch (every warp takes its share of
+// each group).
+template <typename VT, typename XT, typename YT, typename ACC>
+__global__ void __launch_bounds__(256, (slot_min_ctas<9, VT, true>())) k_slot_mixed(const SlotParams p7, const SlotParams p9) {
+    static_assert(sizeof(ACC) == 8, "row buffer entries are 8 bytes");
+    __shared__ ACC s_rows[8][kWarpRowCap];
+    const int wib = threadIdx.x >> 5;
+    slot_loop<7, VT, XT, YT, ACC, false, true>(p7, s_rows[wib], blockIdx.x * 8 + wib, gridDim.x * 8);
+    __syncwarp();
+    slot_loop<9, VT, XT, YT, ACC, false, true>(p9, s_rows[wib], blockIdx.x * 8 + wib, gridDim.x * 8);
+}
+
+template <typename VT, typename XT, typename YT, typename ACC>
+struct SlotKernelMixed {
+    static cudaError_t launch(const SlotParams &p7, const SlotParams &p9, cudaStream_t s) {
+        static int cached = -1, cached_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cached < 0 || cached_dev != dev) {
+            int per_sm = 0, sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_slot_mixed<VT, XT, YT, ACC>, 256, 0) !=
+                cudaSuccess)
+                return cudaErrorInvalidConfiguration;
+            cached = per_sm * sms;
+            cached_dev = dev;
+        }
+        const int n = p7.n_chunks > p9.n_chunks ? p7.n_chunks : p9.n_chunks;
+        if (n <= 0) return cudaSuccess;
+        const int want = (n + 7) / 8;
+        k_slot_mixed<VT, XT, YT, ACC><<<want < cached ? want : cached, 256, 0, s>>>(p7, p9);
+        return cudaGetLastError();
+    }
+};
 
 // Staged-values variant (TV).  The values of each chunk (32E contiguous
 // elements of the slot-major copy) arrive by one 1-D bulk copy (cp.async.bulk,

@@ -109,6 +109,20 @@ def bytes_backward(n_rows: int, n_cols: int, nnz: int, grad_x: bool = True,
     return int(b)
 
 
+def bytes_symmetric(n: int, nnz_upper: int, nnz_strict: int, implementation: bool = False) -> int:
+    """Symmetric CRS (Sect. 1.3.1): the upper triangle with the diagonal read once
+    (value + column index per stored entry), row_ptr, x read once, y written once
+    -- the single-pass scheme whose traffic the paper expects to halve.  With
+    ``implementation`` the two passes this library runs: the upper triangle's
+    row sums, then the transposed strictly upper part (row_ptr, row index and
+    value position per entry, the value read through that position, x read
+    again, y read and written again)."""
+    b = 12 * nnz_upper + 4 * (n + 1) + 8 * n + 8 * n
+    if implementation:
+        b += (4 + 4 + 8) * nnz_strict + 4 * (n + 1) + 8 * n + 16 * n
+    return int(b)
+
+
 def flops(nnz: int, nrhs: int = 1) -> int:
     """Two flops per entry and right-hand side (Sect. 1.2)."""
     return int(2 * nnz * nrhs)

@@ -88,6 +88,29 @@ class Matrix:
         return cls(h, n_rows, n_cols, nnz,
                    torch.float64 if store == abi.SPMV_F64 else torch.float32, device)
 
+    @classmethod
+    def from_symmetric_upper(cls, row_ptr, col_idx, val, dtype: Optional[torch.dtype] = None,
+                             device="cuda") -> "Matrix":
+        """Symmetric CRS: a symmetric n x n matrix from its upper triangle with
+        the diagonal (host numpy arrays; every column >= its row).  apply()
+        computes y = alpha*A*x + beta*y with each off-diagonal value stored once."""
+        device = torch.device(device)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        v = np.ascontiguousarray(val)
+        if v.dtype not in (np.float64, np.float32):
+            v = v.astype(np.float64)
+        if dtype is not None:
+            v = v.astype(np.float64 if dtype == torch.float64 else np.float32)
+        vt = abi.SPMV_F64 if v.dtype == np.float64 else abi.SPMV_F32
+        n, nnz = rp.size - 1, ci.size
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            abi.check(abi.spmv_create_symmetric(ctypes.byref(h), n, nnz, _hptr(rp), _hptr(ci) if nnz else None,
+                                                _hptr(v) if nnz else None, vt, 0, _stream()),
+                      "spmv_create_symmetric")
+        return cls(h, n, n, nnz, torch.float64 if vt == abi.SPMV_F64 else torch.float32, device)
+
     # -- lifetime ---------------------------------------------------------------
     def close(self):
         if self._h is not None and self._h.value:
@@ -274,7 +297,11 @@ class Batch:
     def info(self) -> dict:
         plan = (ctypes.c_int32 * 4)()
         abi.check(abi.spmv_batched_get_info(self._h, plan), "spmv_batched_get_info")
-        return dict(zip(("E", "threads", "tiles", "grid"), list(plan)))
+        out = dict(zip(("E", "threads", "tiles", "grid"), list(plan)))
+        per = (ctypes.c_int32 * len(self.mats))()
+        abi.check(abi.spmv_batched_get_member_plan(self._h, per), "spmv_batched_get_member_plan")
+        out["member_E"] = list(per)
+        return out
 
     def apply(self, xs: Sequence[torch.Tensor], ys: Sequence[torch.Tensor], alpha: float = 1.0,
               beta: float = 0.0, stream=None) -> None:

@@ -394,3 +394,30 @@ def column_heavy_csr(n_rows: int, n_cols: int, seed: int, dense: int = 1, medium
     rp = _row_ptr_from_counts(counts)
     col = np.array([c for r in per_row for c in r], np.int32)
     return CRS(rp, col, rng.standard_normal(col.size), n_cols)
+
+
+def upper_triangle(A: CRS) -> CRS:
+    """The entries of A with col >= row (the upper triangle with the diagonal),
+    row by row in A's order: the stored form of a symmetric matrix."""
+    rows = np.repeat(np.arange(A.n_rows, dtype=np.int64), np.diff(A.row_ptr.astype(np.int64)))
+    keep = A.col_idx[: A.nnz] >= rows
+    counts = np.bincount(rows[keep], minlength=A.n_rows)
+    return CRS(_row_ptr_from_counts(counts), A.col_idx[: A.nnz][keep].copy(), A.val[: A.nnz][keep].copy(), A.n_cols)
+
+
+def random_symmetric_upper(n: int, seed: int, max_len: int = 8, integer: bool = False, empty_frac: float = 0.1) -> CRS:
+    """Upper triangle with diagonal of a random symmetric n x n matrix: some rows
+    without a diagonal, some empty, repeated (row, col) entries, unsorted columns."""
+    rng = np.random.default_rng(seed)
+    per_row = []
+    for i in range(n):
+        k = int(rng.integers(0, max_len + 1)) if rng.random() >= empty_frac else 0
+        cols = list(rng.integers(i, n, k)) if n - i > 0 else []
+        if cols and rng.random() < 0.2:
+            cols.append(cols[0])  # a repeated entry
+        rng.shuffle(cols)
+        per_row.append(cols)
+    counts = np.array([len(r) for r in per_row], np.int64)
+    col = np.array([c for r in per_row for c in r], np.int32)
+    val = rng.integers(-4, 5, col.size).astype(np.float64) if integer else rng.standard_normal(col.size)
+    return CRS(_row_ptr_from_counts(counts), col, val, n)

@@ -92,3 +92,24 @@ def test_tiler_and_tuner_are_host_logic():
     """The binding refuses to run without the library, and there is no CPU path."""
     import paper_1106_5908_gb300.torch_api as api
     assert not hasattr(api, "cpu_apply")
+
+
+def test_symmetric_create_rejects_lower_entries_on_host(lib):
+    """spmv_create_symmetric takes the upper triangle: an entry left of the
+    diagonal, or any CRS mistake, is rejected before the device is touched."""
+    from paper_1106_5908_gb300 import _abi
+
+    def create(n, rp, ci):
+        h = ctypes.c_void_p()
+        rp = np.ascontiguousarray(rp, np.int32)
+        ci = np.ascontiguousarray(ci, np.int32)
+        val = np.ones(max(ci.size, 1))
+        return lib.spmv_create_symmetric(ctypes.byref(h), n, int(ci.size), rp.ctypes.data_as(ctypes.c_void_p),
+                                         ci.ctypes.data_as(ctypes.c_void_p), val.ctypes.data_as(ctypes.c_void_p),
+                                         _abi.SPMV_F64, 0, None)
+    assert create(3, [0, 2, 3, 4], [0, 2, 0, 2]) == _abi.SPMV_ERR_INVALID_INDEX   # (1, 0) lies below
+    assert create(3, [0, 2, 3, 4], [0, 3, 1, 2]) == _abi.SPMV_ERR_INVALID_INDEX   # column out of range
+    assert create(3, [1, 2, 3, 4], [0, 2, 1, 2]) == _abi.SPMV_ERR_INVALID_INDEX   # row_ptr[0] != 0
+    assert lib.spmv_create_symmetric(None, 3, 0, None, None, None, 0, 0, None) == _abi.SPMV_ERR_INVALID_ARG
+    assert lib.spmv_create_symmetric(ctypes.byref(ctypes.c_void_p()), -1, 0, None, None, None, 0, 0,
+                                     None) == _abi.SPMV_ERR_INVALID_ARG

@@ -18,7 +18,8 @@ FUNCS = ("oracle_spmv", "oracle_spmv_omp", "oracle_num_threads", "oracle_spmm", 
          "oracle_backward", "oracle_split_blocks", "oracle_split_halo", "oracle_cg",
          "oracle_row_histogram", "oracle_thread_rows", "oracle_spmv_f32", "oracle_spmv_split",
          "oracle_node_create", "oracle_node_destroy", "oracle_node_spmv", "oracle_node_spmv_f32",
-         "oracle_node_spmv_split", "oracle_node_set_y", "oracle_node_get_y", "oracle_node_threads")
+         "oracle_node_spmv_split", "oracle_node_set_y", "oracle_node_get_y", "oracle_node_threads",
+         "oracle_spmv_sym")
 
 
 @contextlib.contextmanager
@@ -67,6 +68,11 @@ NODE_PINS = [
 SPLIT_PINS = [
     lambda: npins.test_spmv_split_literal_and_plain((64, 64), 3),
     lambda: npins.test_spmv_split_integer_exact(),
+]
+
+SYM_PINS = [
+    lambda: pins.test_spmv_sym_vs_dense_and_full(64, 1),
+    lambda: pins.test_spmv_sym_integer_exact_and_laplacians(),
 ]
 
 MUTANTS = {
@@ -135,6 +141,13 @@ MUTANTS = {
     "node split reads the halo one position off": ("acc = acc + nd->valn[k] * nd->halo[nd->cin[k]];",
                                                    "acc = acc + nd->valn[k] * nd->halo[nd->cin[k] > 0 ? nd->cin[k] - 1 : 0];",
                                                    NODE_PINS),
+    # symmetric CRS (Sect. 1.3.1)
+    "symmetric form counts the diagonal twice": ("            if (j != i) {\n                double q = val[k] * x[i];",
+                                                 "            if (1) {\n                double q = val[k] * x[i];",
+                                                 SYM_PINS),
+    "symmetric form mirrors with x[j]": ("double q = val[k] * x[i];", "double q = val[k] * x[j];", SYM_PINS),
+    "symmetric form drops the mirrored entry": ("                t[j] = t[j] + q;", "                t[j] = t[j] + 0.0 * q;",
+                                                SYM_PINS),
     # CG
     "CG update with the wrong sign": ("r[i] = r[i] - a * q[i];", "r[i] = r[i] + a * q[i];",
                                       [lambda: pins.test_cg_solves_spd()]),

@@ -352,3 +352,47 @@ def test_row_histogram():
     lens = np.diff(A.row_ptr)
     ref = np.bincount(np.minimum(lens, 39), minlength=40)
     assert np.array_equal(h, ref)
+
+
+def expand_symmetric(U):
+    """Full CRS of U + U_s^T (U_s: U without its diagonal), entries summed."""
+    import scipy.sparse as sp
+    n = U.n_rows
+    M = sp.csr_matrix((U.val, U.col_idx, U.row_ptr), shape=(n, n))
+    D = sp.diags(M.diagonal())
+    F = (M + M.T - D).tocsr()
+    F.sum_duplicates()
+    F.sort_indices()
+    return W.CRS(F.indptr.astype(np.int32), F.indices.astype(np.int32), F.data, n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 64, 300])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_spmv_sym_vs_dense_and_full(n, seed):
+    U = W.random_symmetric_upper(n, seed)
+    x = W.uniform(n, seed + 10)
+    y0 = W.uniform(n, seed + 20)
+    D = dense_of(U)
+    full = D + np.triu(D, 1).T
+    F = expand_symmetric(U)
+    for alpha, beta in [(1.0, 0.0), (-0.5, 1.0), (2.0, -3.0), (0.0, 1.5)]:
+        y, bound = oracle.spmv_sym(*U.astuple(), x, alpha, beta, y0, with_bound=True)
+        ref = alpha * (full @ x) + (beta * y0 if beta != 0 else 0.0)
+        assert within(y, ref, bound, 1e-13)
+        yf, bf = oracle.spmv(*F.astuple(), x, alpha, beta, y0, with_bound=True)
+        assert within(y, yf, bound, 1e-13)
+
+
+def test_spmv_sym_integer_exact_and_laplacians():
+    for A in (W.laplace2d(12), W.laplace3d(6), W.hamiltonian_like(3000, seed=7)):
+        U = W.upper_triangle(A)
+        x = W.integers(A.n_rows, 5).astype(np.float64)
+        if A.n_rows == 3000:  # random values: tolerance; the stencils: exact
+            y, bound = oracle.spmv_sym(*U.astuple(), x, with_bound=True)
+            assert within(y, oracle.spmv(*A.astuple(), x), bound, 1e-13)
+        else:
+            assert np.array_equal(oracle.spmv_sym(*U.astuple(), x), oracle.spmv(*A.astuple(), x))
+    Ui = W.random_symmetric_upper(200, 3, integer=True)
+    xi = W.integers(200, 6).astype(np.float64)
+    Fi = expand_symmetric(Ui)
+    assert np.array_equal(oracle.spmv_sym(*Ui.astuple(), xi), oracle.spmv(*Fi.astuple(), xi))
