@@ -45,8 +45,8 @@ FP64_FMA_PER_S = 598e9
 # DRAM traffic of one launch of the plain FP64 chunk kernel on this workload, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel source whose hash is recorded with it.
-TRAFFIC = {"kernel_hash": "87a96c5fe6f5910d", "bytes_per_launch": 753408256,
-           "source": "profiles/k_slot_f64_hamiltonian_4194304.md (one launch, --set full)"}
+TRAFFIC = {"kernel_hash": "26b9e58772057f9b", "bytes_per_launch": 751086165,
+           "source": "profiles/k_slot_f64_hamiltonian_4194304.md (mean of three launches, DRAM counters)"}
 
 
 def kernel_hash() -> str:
@@ -439,7 +439,8 @@ def run_ours(args, rank, world, local_rank):
                   "split_f64": {"ms": form_ms["split"], "GBs": b_split / form_ms["split"] / 1e6,
                                 "GFLOPs": model.flops(nnz) / form_ms["split"] / 1e6,
                                 "time_vs_plain": form_ms["split"] / form_ms["plain"],
-                                "model_eq2_vs_eq1": model.split_penalty(nnz / n) + 1},
+                                "model_eq2_vs_eq1": model.split_penalty(nnz / n) + 1,
+                                "bytes_with_halo_vs_plain": b_split / b_plain},
                   "fp32_storage": {"ms": form_ms["f32"], "GBs": b_f32 / form_ms["f32"] / 1e6,
                                    "GFLOPs": model.flops(nnz) / form_ms["f32"] / 1e6,
                                    "time_vs_plain": form_ms["f32"] / form_ms["plain"]},
@@ -655,7 +656,7 @@ def run_only_plain(args, local_rank):
     from paper_1106_5908_gb300.build import build as build_lib
     torch.cuda.set_device(local_rank)
     build_lib()
-    if args.only in ("backward27", "split", "batch256"):
+    if args.only in ("backward27", "split", "batch256", "ircg160"):
         run_only_form(args, local_rank)
         return
     f32 = args.only == "plain32"
@@ -692,7 +693,8 @@ def run_only_form(args, local_rank):
     """One form alone, warm-up plus K calls (kernel profiling cases):
     `--only backward27` the reverse pass (grad_x and grad_val) on the 128^3
     27-point matrix, `--only split` the split product (8 blocks, two streams) on
-    the Hamiltonian-like matrix, `--only batch256` the 256-matrix batch."""
+    the Hamiltonian-like matrix, `--only batch256` the 256-matrix batch, `--only
+    ircg160` one IR-CG solve on the 160^3 7-point matrix per call."""
     import torch
     from paper_1106_5908_gb300 import Batch, Matrix
     from paper_1106_5908_gb300.build import build as build_lib
@@ -712,6 +714,12 @@ def run_only_form(args, local_rank):
         y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
         s2 = torch.cuda.Stream()
         fn = lambda: sp.apply(x, y, s_comm=s2)
+    elif args.only == "ircg160":
+        from paper_1106_5908_gb300 import ir_cg
+        A = W.laplace3d(W.POISSON7_GRID)
+        M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+        b = torch.as_tensor(W.uniform(A.n_rows, W.SEED_POISSON7_B)).cuda()
+        fn = lambda: ir_cg(M, b, outer_tol=1e-12, max_outer=50, inner_tol=1e-3, max_inner=500)
     else:
         sizes = W.batch_sizes(W.BATCH_COUNT)
         mats, xs, ys = [], [], []
@@ -797,10 +805,11 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "stencil27", "backward27", "split",
-                                       "batch256"), default=None,
+                                       "batch256", "ircg160"), default=None,
                     help="run only the plain FP64 product on the Hamiltonian-like matrix (plain32: its "
                          "FP32-storage product), the 7-point or the 27-point matrix, or one form: the reverse "
-                         "pass on the 27-point matrix, the split product, the 256-matrix batch (kernel profiling)")
+                         "pass on the 27-point matrix, the split product, the 256-matrix batch, one IR-CG "
+                         "solve on the 7-point matrix (kernel profiling)")
     ap.add_argument("--study", choices=("ordering",), default=None,
                     help="natural / RCM / random ordering of the Hamiltonian-like matrix")
     ap.add_argument("--study-auto-only", action="store_true",

@@ -137,6 +137,9 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  *           into chunk-major, lane-interleaved order and loaded coalesced into
  *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 9, 15);
  *           the copy is built on first use and its values follow spmv_set_values;
+ *           with FP32 storage and E = 7 or 9 the default accumulator sums each
+ *           lane's piece of a row (at most E entries) with FP32 FMAs and joins
+ *           the pieces in float-float (see spmv_set_accumulator);
  * family 5: sorted row-slice kernel (SELL-C-sigma with C = 64: in each window
  *           of param rows, a power of two from 32 to 2^20, default 4096, the
  *           rows ordered by length and stored 64 rows at a time, two rows per
@@ -155,23 +158,29 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
 spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
 /* Accumulator of an FP32-storage handle: 0 = one FP64 FMA per entry (operands
- * widened exactly), 1 = exact-product float-float accumulation on the FP32 pipe
- * (default; relative accuracy about 2^-44 of sum |a_ij x_j|).  The float-float
- * sum splits each product exactly only inside FP32's range: a row with a nonzero
- * product below 2^-100 in magnitude, an overflow of a product or of the running
- * sum, or an infinite or NaN operand is summed again with FP64 FMAs (one more
- * pass over that row's entries), so both settings give FP64-accumulation results
- * for every input.  FP64 handles always accumulate with FP64 FMAs and ignore
- * this setting. */
+ * widened exactly), 1 = FP32-pipe accumulation (default).  Setting 1 is, in the
+ * slot-major kernel with E = 7 or 9 (family 4 and the batched launch), FP32
+ * FMA runs over each lane's piece of a row (at most 9 products: error at most
+ * gamma_9 = 9u/(1-9u) ~ 5.4e-7 of sum |a_ij x_j|, u = 2^-24) joined across lanes
+ * by two-sum; a row whose FP32 sum is not finite or below 2^-100 in magnitude
+ * is summed again with FP64 FMAs.  Everywhere else it is exact-product
+ * float-float accumulation (relative accuracy about 2^-44 of sum |a_ij x_j|),
+ * which splits each product exactly only inside FP32's range: a row with a
+ * nonzero product below 2^-100 in magnitude, an overflow of a product or of the
+ * running sum, or an infinite or NaN operand is summed again with FP64 FMAs.
+ * Either way every row is within 1e-6 * sum_j |a_ij x_j| of the FP64-accumulated
+ * sum for every input (one more pass over a row's entries where the FP32 form
+ * cannot guarantee it).  FP64 handles always accumulate with FP64 FMAs and
+ * ignore this setting. */
 spmv_status spmv_set_accumulator(spmv_handle h, int32_t acc);
 
 /* Plain spMVM, Listing 1 generalised: y = alpha*A*x + beta*y.
  * x: n_cols entries of type xt; y: n_rows entries of type yt.  Supported
  * (value, x, y) types: (F64, F64, F64), (F32, F32, F32), (F32, F32, F64).  FP32
- * operands: every product of two floats is exact, and the row sums carry at
- * least 44 significant bits (float-float, see spmv_set_accumulator) over FP64's
- * exponent range (rows outside FP32's go through FP64 FMAs), within
- * 1e-6 * sum_j |a_ij x_j| of the FP64 sum; an FP32 y is then rounded once.
+ * operands: the row sums are within 1e-6 * sum_j |a_ij x_j| of the FP64 sum of
+ * the exact products over FP64's exponent range (FP32 runs or float-float, see
+ * spmv_set_accumulator; rows outside FP32's range go through FP64 FMAs); an
+ * FP32 y is then rounded once.
  * x and y must not overlap. */
 spmv_status spmv_apply(spmv_handle h, double alpha, const void *x, spmv_dtype xt,
                        double beta, void *y, spmv_dtype yt, void *stream);

@@ -387,6 +387,7 @@ struct spmv_matrix {
     std::vector<int32_t> h_rp;
     // plan
     double col_random = 0.0;  // column_randomness() of the pattern
+    int32_t max_row = 0x7fffffff;  // longest row (set by the tuner)
     int family = 0;  // 0 warp chunks, 1 row-vector, 2 staged tiles, 3 three-stage chunks
     int E = 16;      // entries per lane (family 0) or per thread segment (family 2)
     int T = 8;
@@ -549,6 +550,8 @@ constexpr double kBatchSlotMeanE9 = 4.0;
 
 void autotune(spmv_matrix *h) {
     const double mean = h->n_rows ? static_cast<double>(h->nnz) / h->n_rows : 0.0;
+    h->max_row = 0;
+    for (int32_t i = 0; i < h->n_rows; ++i) h->max_row = std::max(h->max_row, h->h_rp[i + 1] - h->h_rp[i]);
     int T = 1;
     while (T < 32 && T < mean * 0.5) T <<= 1;
     h->T = T;
@@ -562,7 +565,8 @@ void autotune(spmv_matrix *h) {
         h->family = 4;
         h->E = (mean < 8.0) ? 7 : 9;
     }
-    if (!scattered && mean >= kSellMinRowLength && h->sell_pad <= kSellMaxPadding) h->family = 5;
+    if (!scattered && h->sell_pad <= kSellMaxPadding && (h->vk == kF32 || mean >= kSellMinRowLength))
+        h->family = 5;
 }
 
 // Share of entries (sampled rows) whose column is more than 8 away from every
@@ -669,7 +673,7 @@ SellTable *get_sell(spmv_matrix *h, int32_t sigma, cudaStream_t s, bool transpos
         t.n = static_cast<int32_t>(d.size());
         SellOps o;
         const int acc = (h->vk == kF32) ? kAccFF : kAccF64;
-        t.n_ctas = sell_ops(h->vk, h->vk, h->vk, acc, &o) ? o.ctas_for(t.n) : 0;
+        t.n_ctas = sell_ops(h->vk, h->vk, h->vk, acc, &o, transposed ? 0x7fffffff : h->max_row) ? o.ctas_for(t.n) : 0;
         if (t.n_ctas <= 0) return nullptr;
         std::vector<int32_t> ws;
         sell_ranges(d, h_rp, t.n_ctas, ws);
@@ -843,7 +847,7 @@ spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, doub
     if (h->family == 5 && !h->d_rmap) {
         SellOps lops;
         SellTable *lt = nullptr;
-        if (sell_ops(h->vk, xk, yk, acc, &lops) && (lt = get_sell(h, h->sigma, s)) != nullptr) {
+        if (sell_ops(h->vk, xk, yk, acc, &lops, h->max_row) && (lt = get_sell(h, h->sigma, s)) != nullptr) {
             SellParams lp{};
             lp.slices = lt->d;
             lp.srows = lt->srows;
@@ -1030,7 +1034,8 @@ spmv_status ensure_mirror32(spmv_matrix *h, cudaStream_t s) {
 static spmv_status ready_for_capture(spmv_matrix *h, int xk, int yk) {
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
     SellOps lops;
-    if (h->family == 5 && !h->d_rmap && sell_ops(h->vk, xk, yk, acc, &lops) && get_sell(h, h->sigma, nullptr))
+    if (h->family == 5 && !h->d_rmap && sell_ops(h->vk, xk, yk, acc, &lops, h->max_row) &&
+        get_sell(h, h->sigma, nullptr))
         return cudaDeviceSynchronize() == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
     SlotOps sops;
     if ((h->family == 4 || h->family == 5 || h->family == 6) &&

@@ -181,6 +181,43 @@ struct AccFF {
     __device__ __forceinline__ double get() const { return widen(h) + widen(l); }
 };
 
+// FP32 runs with float-float carries, for kernels whose lanes own at most
+// kFRMaxRun consecutive entries of a row (the slot-major chunk kernel with
+// E <= 9): the products of one lane's piece of a row are summed by plain FP32
+// FMAs (recursive summation, error at most gamma_k sum |a_ij x_j| with k <= 9
+// terms, gamma_k = k u / (1 - k u), u = 2^-24: 5.4e-7, inside the 1e-6 FP32-storage
+// tolerance), and the pieces of a row cut by lane boundaries are combined by
+// two-sum (float-float), whose error is of order u^2.  The bound assumes no
+// partial sum underflows or overflows; a row whose final sum is not finite or
+// below kFFTiny in magnitude (a sum that small can only come from terms that
+// small, or from exact cancellation) is marked poisoned and summed again with
+// FP64 products, as for AccFF.  Each entry costs one FP32 FMA instead of
+// AccFF's ten-odd FP32 operations.
+constexpr int kFRMaxRun = 9;
+struct AccFR {
+    float h, l;
+    __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }
+    __device__ __forceinline__ void fma(float v, float x) { h = fmaf(v, x, h); }
+    __device__ __forceinline__ void add(const AccFR &o) {
+        const float s = h + o.h;
+        const float bb = s - h;
+        const float e = (h - (s - bb)) + (o.h - bb);
+        h = s;
+        l = l + (e + o.l);
+    }
+    __device__ __forceinline__ bool poisoned() const {
+        const float a = fabsf(h);
+        return !(a >= kFFTiny && a <= 0x1.fffffep127f) || l != l;
+    }
+    __device__ __forceinline__ double get() const { return widen(h) + widen(l); }
+};
+
+// Accumulator for work that is not cut into pieces of at most kFRMaxRun
+// entries (whole rows per lane, long rows strided over a warp): AccFR falls back
+// to AccFF there.
+template <typename ACC> struct WholeRowAcc { using type = ACC; };
+template <> struct WholeRowAcc<AccFR> { using type = AccFF; };
+
 // Row r of m summed again with exact FP64 products of its (FP32-stored)
 // operands, in CRS order: the fallback for a poisoned float-float row sum (see
 // AccFF).  x[j] is read at x + j*ldx.
@@ -203,7 +240,7 @@ __device__ __forceinline__ double row_sum_exact(const MatRef m, int64_t r, const
 // again from the CRS arrays of m (row r, operand x); anything else as it is.
 template <typename VT, bool INDIRECT, typename XT, typename ACC>
 __device__ __forceinline__ double acc_value(const ACC &a, const MatRef &m, int64_t r, const XT *__restrict__ x) {
-    if constexpr (std::is_same<ACC, AccFF>::value) {
+    if constexpr (std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value) {
         if (a.poisoned()) return row_sum_exact<VT, INDIRECT>(m, r, x);
     }
     return a.get();

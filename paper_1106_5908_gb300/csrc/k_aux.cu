@@ -97,7 +97,9 @@ cudaError_t launch_rowvec(const KParams &p, const int32_t n_rows, int vk, int xk
 // nonlocal column a block needs is copied into the contiguous halo buffer.
 // ---------------------------------------------------------------------------
 // halo[h] = x[map[h]]: each thread takes four entries a blockDim apart per
-// step, so four map loads and then four x gathers are in flight at once.
+// step, so four map loads and then four x gathers are in flight at once.  (The
+// halo stored evict-last in L2 and read back evict-first by the nonlocal part:
+// split 248.7 against 232-235 us, dropped.)
 __global__ void __launch_bounds__(256) k_gather(const double *__restrict__ x,
                                                 const int32_t *__restrict__ map,
                                                 double *__restrict__ halo, int64_t n) {

@@ -1,15 +1,21 @@
 // Compiled configurations of the sorted row-slice kernel (plan family 5) and its
-// relayout kernel: FP64 values and vectors, and FP32 storage with float-float
-// accumulation.
+// relayout kernel: FP64 values and vectors, and FP32 storage with FP32 runs
+// (every row at most 9 entries, so a lane's chain over a row is a run) or
+// float-float accumulation.
 #include "internal.h"
 #include "sell_kernel.cuh"
 
 namespace spmv {
 
-bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops) {
+bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops, int32_t max_row) {
     if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64) {
         ops->launch = &SellKernel<double, double, double, AccF64>::launch;
         ops->ctas_for = &SellKernel<double, double, double, AccF64>::ctas_for;
+        return true;
+    }
+    if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF && max_row <= kFRMaxRun) {
+        ops->launch = &SellKernel<float, float, float, AccFR>::launch;
+        ops->ctas_for = &SellKernel<float, float, float, AccFR>::ctas_for;
         return true;
     }
     if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF) {

@@ -1,6 +1,7 @@
 // Compiled configurations of the slot-major chunk kernel (plan family 4) and its
-// relayout kernel: FP64 values and vectors, and FP32 storage with float-float
-// accumulation.
+// relayout kernel: FP64 values and vectors, and FP32 storage with FP32 runs and
+// float-float carries (E = 7, 9: at most 9 entries of a row per lane) or
+// float-float accumulation (E = 15).
 #include "internal.h"
 #include "slot_kernel.cuh"
 
@@ -16,11 +17,11 @@ bool slot_ops_batched(int vk, int acc, int E, SlotOps *ops) {
         return true;
     }
     if (vk == kF32 && acc == kAccFF && E == 7) {
-        ops->launch = &SlotKernel<7, float, float, float, AccFF, false, true>::launch;
+        ops->launch = &SlotKernel<7, float, float, float, AccFR, false, true>::launch;
         return true;
     }
     if (vk == kF32 && acc == kAccFF && E == 9) {
-        ops->launch = &SlotKernel<9, float, float, float, AccFF, false, true>::launch;
+        ops->launch = &SlotKernel<9, float, float, float, AccFR, false, true>::launch;
         return true;
     }
     return false;
@@ -45,8 +46,8 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     SPMV_S(kF64, kF64, kF64, kAccF64, 9, double, double, double, AccF64)
     SPMV_S(kF64, kF64, kF64, kAccF64, 11, double, double, double, AccF64)
     SPMV_S(kF64, kF64, kF64, kAccF64, 15, double, double, double, AccF64)
-    SPMV_S(kF32, kF32, kF32, kAccFF, 7, float, float, float, AccFF)
-    SPMV_S(kF32, kF32, kF32, kAccFF, 9, float, float, float, AccFF)
+    SPMV_S(kF32, kF32, kF32, kAccFF, 7, float, float, float, AccFR)
+    SPMV_S(kF32, kF32, kF32, kAccFF, 9, float, float, float, AccFR)
     SPMV_S(kF32, kF32, kF32, kAccFF, 15, float, float, float, AccFF)
 #undef SPMV_S
     return false;
@@ -54,7 +55,7 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
 
 cudaError_t launch_slot_mixed(int vk, int acc, const SlotParams &p7, const SlotParams &p9, cudaStream_t s) {
     if (vk == kF64 && acc == kAccF64) return SlotKernelMixed<double, double, double, AccF64>::launch(p7, p9, s);
-    if (vk == kF32 && acc == kAccFF) return SlotKernelMixed<float, float, float, AccFF>::launch(p7, p9, s);
+    if (vk == kF32 && acc == kAccFF) return SlotKernelMixed<float, float, float, AccFR>::launch(p7, p9, s);
     return cudaErrorInvalidValue;
 }
 

@@ -83,7 +83,8 @@ __device__ __forceinline__ void sell_fma_tail(ACC (&acc)[kSellK], const VT (&v)[
 template <typename VT, typename XT, typename YT, typename ACC>
 __device__ __forceinline__ void sell_store(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y, int row,
                                            const ACC &a, double alpha, double beta, bool plain, double old) {
-    if constexpr (std::is_same<ACC, AccFF>::value && std::is_same<YT, float>::value) {
+    if constexpr ((std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value) &&
+                  std::is_same<YT, float>::value) {
         if (plain && !a.poisoned()) {
             y[row] = a.h + a.l;
             return;

@@ -91,7 +91,7 @@ __device__ __forceinline__ void store_row(YT *__restrict__ y, int64_t row, doubl
 template <typename VT, bool INDIRECT, typename XT, typename YT, typename ACC>
 __device__ __forceinline__ void store_acc(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y,
                                           int64_t row, const ACC &a, double alpha, double beta, bool plain) {
-    if constexpr (std::is_same<ACC, AccFF>::value) {
+    if constexpr (std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value) {
         if (a.poisoned()) {
             store_row(y, row, row_sum_exact<VT, INDIRECT>(m, row, x), alpha, beta, plain, m.rmap);
             return;
@@ -170,6 +170,12 @@ __device__ __forceinline__ AccFF shfl_up_acc(const AccFF &a, int d) {
     b.l = __shfl_up_sync(0xffffffffu, a.l, d);
     return b;
 }
+__device__ __forceinline__ AccFR shfl_up_acc(const AccFR &a, int d) {
+    AccFR b;
+    b.h = __shfl_up_sync(0xffffffffu, a.h, d);
+    b.l = __shfl_up_sync(0xffffffffu, a.l, d);
+    return b;
+}
 __device__ __forceinline__ AccF64 shfl_xor_acc2(const AccF64 &a, int d) {
     AccF64 b;
     b.s = __shfl_xor_sync(0xffffffffu, a.s, d);
@@ -187,7 +193,7 @@ template <typename VT, typename XT, typename YT, typename ACC, bool INDIRECT>
 __device__ __forceinline__ void long_row(const MatRef &m, const ChunkDesc &d, const XT *__restrict__ x,
                                          YT *__restrict__ y, double alpha, double beta, bool plain,
                                          int lane) {
-    ACC acc;
+    typename WholeRowAcc<ACC>::type acc;
     acc.zero();
     for (int k = d.k0 + lane; k < d.k1; k += 32) {
         const XT xv = __ldg(x + __ldg(m.col + k));
@@ -207,7 +213,7 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
                                               YT *__restrict__ y, double alpha, double beta, bool plain,
                                               int lane) {
     for (int r = r0 + lane; r < r1; r += 32) {
-        ACC acc;
+        typename WholeRowAcc<ACC>::type acc;
         acc.zero();
         const int kb = __ldg(m.rp + r), ke = __ldg(m.rp + r + 1);
         for (int k = kb; k < ke; ++k) {
@@ -224,11 +230,12 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
 // One lane's share of a regular chunk.  vals/xv hold the lane's E slots (zero in
 // slots outside [lo, hi)); bit e of mbits is set where a row starts in slot e;
 // `ends` says whether the lane's last row ends with its slots.  The FMA chain
-// restarts at every row start (a register select, no branch) and the running sum
-// of the current row is stored to the row buffer after every entry once the row
-// is known to have started in this lane, so the last store of a row is its full
-// sum.  The part of the first row that started in an earlier lane is combined in
-// lane order with the carries of those lanes (one FP64 add per crossing).
+// restarts at every row start (a register select, no branch); a row that starts
+// and ends in this lane is in the row buffer once its last slot is done (FP64:
+// stored at that slot only; float-float: stored after every slot).  The part of
+// the first row that started in an earlier lane is combined in lane order with
+// the carries of those lanes (one add per crossing) and stored by the lane where
+// the row ends.
 // `pre` is the number of rows starting in the chunk before this lane's slots.
 template <int E, typename VT, typename XT, typename ACC>
 __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
@@ -239,6 +246,17 @@ __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&x
     int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
     const int first_row = row;
     const uint32_t flush = active ? (mbits & ~(1u << lo)) : 0u;
+    // slots in [lo, hi) after which a row ends: the next slot starts one, or the
+    // slot is the lane's last and `ends`
+    const uint32_t span = active ? ((hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u)) : 0u;
+    const uint32_t endm = ((mbits >> 1) | ((active && ends) ? (1u << (hi - 1)) : 0u)) & span;
+    // FP64 and FP32-run sums store at row ends only (fewer shared-memory
+    // wavefronts for a kernel bound by L1TEX and the FP64 pipe: C2 150.4 ->
+    // 149.9 us, E = 11 163.8 -> 156.5 us); the float-float kernels, bound by
+    // instruction issue, store after every slot once the row has started (the
+    // row-end test costs them 3-6 %), so the last store of a row is its full sum
+    constexpr bool kRowEndStores = !std::is_same<ACC, AccFF>::value;
+    static_assert(!std::is_same<ACC, AccFR>::value || E <= kFRMaxRun, "FP32 runs of at most kFRMaxRun entries");
     ACC acc;
     acc.zero();
     ACC pend;
@@ -255,7 +273,7 @@ __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&x
         row += b ? 1 : 0;
         started = started || b;
         acc.fma(vals[e], xv[e]);
-        if (started) srow[row - r0] = acc;
+        if (kRowEndStores ? (started && ((endm >> e) & 1u)) : started) srow[row - r0] = acc;
     }
     if (active && !started && ends) {
         pend = acc;

@@ -194,11 +194,11 @@ def test_laplace3d_160_fp32(poisson7):
 
 def test_autotuner_choices():
     """The tuner picks the sorted row-slice kernel (windows of 4096 rows) for
-    matrices whose columns stay near the previous row's (stencils) with at least
-    12 entries per row; otherwise the chunk kernels: FP64 the slot-major one with
-    7 entries per lane for short rows and 9 otherwise, FP32 storage the slot-major
-    one with 9 for scattered columns and the staged one with 15 on stencils.  A
-    matrix whose sorted slices would pad more than 10 % keeps the chunk kernels."""
+    matrices whose columns stay near the previous row's (stencils): in FP64 with
+    at least 12 entries per row, with FP32 storage at any row length; otherwise
+    the chunk kernels: FP64 the slot-major one with 7 entries per lane for short
+    rows and 9 otherwise, FP32 storage the slot-major one with 9.  A matrix whose
+    sorted slices would pad more than 10 % keeps the chunk kernels."""
     from paper_1106_5908_gb300 import Matrix
     H = W.hamiltonian_like(50000, seed=3)
     L3 = W.laplace3d(24)
@@ -206,7 +206,7 @@ def test_autotuner_choices():
     for A, want in ((H, (4, 9)), (L3, (4, 7)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols).info()
         assert (info["family"], info["E"]) == want
-    for A, want in ((H, (4, 9)), (L3, (0, 15)), (S27, (5, 4096))):
+    for A, want in ((H, (4, 9)), (L3, (5, 4096)), (S27, (5, 4096))):
         info = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols, dtype=torch.float32).info()
         assert (info["family"], info["E"]) == want
     # 100 rows of lengths 100, 99, ..., 1 with columns 0 .. len-1 (not scattered,
