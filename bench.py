@@ -650,7 +650,8 @@ def run_only_plain(args, local_rank):
     """Only the plain product, warm-up plus K launches (the case a kernel profiler
     captures): on the Hamiltonian-like matrix (`--only plain`, FP64; `--only
     plain32`, FP32 storage), the 160^3 7-point Poisson matrix (`--only
-    poisson7`) or the 128^3 27-point stencil (`--only stencil27`)."""
+    poisson7`; `--only poisson7_32`, FP32 storage) or the 128^3 27-point stencil
+    (`--only stencil27`)."""
     import torch
     from paper_1106_5908_gb300 import Matrix
     from paper_1106_5908_gb300.build import build as build_lib
@@ -659,10 +660,10 @@ def run_only_plain(args, local_rank):
     if args.only in ("backward27", "split", "batch256", "ircg160"):
         run_only_form(args, local_rank)
         return
-    f32 = args.only == "plain32"
+    f32 = args.only in ("plain32", "poisson7_32")
     if args.only in ("plain", "plain32"):
         A, x = hamiltonian_workload()
-    elif args.only == "poisson7":
+    elif args.only in ("poisson7", "poisson7_32"):
         A = W.laplace3d(W.POISSON7_GRID)
         x = W.uniform(A.n_cols, W.SEED_POISSON7_B)
     else:
@@ -804,10 +805,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "stencil27", "backward27", "split",
-                                       "batch256", "ircg160"), default=None,
+    ap.add_argument("--only", choices=("plain", "plain32", "poisson7", "poisson7_32", "stencil27", "backward27",
+                                       "split", "batch256", "ircg160"), default=None,
                     help="run only the plain FP64 product on the Hamiltonian-like matrix (plain32: its "
-                         "FP32-storage product), the 7-point or the 27-point matrix, or one form: the reverse "
+                         "FP32-storage product), the 7-point (poisson7_32: FP32 storage) or the 27-point "
+                         "matrix, or one form: the reverse "
                          "pass on the 27-point matrix, the split product, the 256-matrix batch, one IR-CG "
                          "solve on the 7-point matrix (kernel profiling)")
     ap.add_argument("--study", choices=("ordering",), default=None,

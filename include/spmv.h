@@ -143,10 +143,11 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  * family 5: sorted row-slice kernel (SELL-C-sigma with C = 64: in each window
  *           of param rows, a power of two from 32 to 2^20, default 4096, the
  *           rows ordered by length and stored 64 rows at a time, two rows per
- *           lane; rows of more than 128 entries summed by a whole warp); FP64
- *           and FP32 storage with float-float accumulation, other combinations
- *           run the slot-major kernel; copy built on first use, values follow
- *           spmv_set_values;
+ *           lane; rows of more than 128 entries summed by a whole warp); FP64,
+ *           and FP32 storage with the default accumulator (FP32 runs: a whole
+ *           row when no row exceeds 9 entries, else blocks of 4 entries folded
+ *           into float-float), other combinations run the slot-major kernel;
+ *           copy built on first use, values follow spmv_set_values;
  * family 6: the slot-major kernel of family 4 with each chunk's values brought
  *           into a two-stage shared-memory ring per warp by 1-D bulk copies
  *           (cp.async.bulk) instead of register loads, so they bypass L1's miss
@@ -162,8 +163,10 @@ spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
  * slot-major kernel with E = 7 or 9 (family 4 and the batched launch), FP32
  * FMA runs over each lane's piece of a row (at most 9 products: error at most
  * gamma_9 = 9u/(1-9u) ~ 5.4e-7 of sum |a_ij x_j|, u = 2^-24) joined across lanes
- * by two-sum; a row whose FP32 sum is not finite or below 2^-100 in magnitude
- * is summed again with FP64 FMAs.  Everywhere else it is exact-product
+ * by two-sum, and in the row-slice kernel (family 5) FP32 FMA runs over a whole
+ * row of at most 9 entries or over blocks of 4 entries folded into float-float
+ * (gamma_4 ~ 2.4e-7); a row whose FP32 sum is not finite or below 2^-100 in
+ * magnitude is summed again with FP64 FMAs.  Everywhere else it is exact-product
  * float-float accumulation (relative accuracy about 2^-44 of sum |a_ij x_j|),
  * which splits each product exactly only inside FP32's range: a row with a
  * nonzero product below 2^-100 in magnitude, an overflow of a product or of the

@@ -212,11 +212,41 @@ struct AccFR {
     __device__ __forceinline__ double get() const { return widen(h) + widen(l); }
 };
 
+// FP32 runs folded into float-float, for a lane that sums a whole row of any
+// length in blocks of at most kFRMaxRun entries (the row-slice kernel): the
+// block's products go into the run r by plain FP32 FMAs, and fold() adds r to
+// the float-float total (h, l) by two-sum and clears it.  Error at most
+// gamma_k sum |a_ij x_j| for blocks of k entries, plus order u^2 from the
+// folds; the same range rule as AccFR (checked after the last fold).
+struct AccFRF {
+    float r, h, l;
+    __device__ __forceinline__ void zero() { r = 0.f; h = 0.f; l = 0.f; }
+    __device__ __forceinline__ void fma(float v, float x) { r = fmaf(v, x, r); }
+    __device__ __forceinline__ void fold() {
+        const float s = h + r;
+        const float bb = s - h;
+        const float e = (h - (s - bb)) + (r - bb);
+        h = s;
+        l = l + e;
+        r = 0.f;
+    }
+    __device__ __forceinline__ bool poisoned() const {
+        const float a = fabsf(h);
+        return !(a >= kFFTiny && a <= 0x1.fffffep127f) || l != l || r != 0.f;
+    }
+    __device__ __forceinline__ double get() const { return widen(h) + widen(l) + widen(r); }
+};
+
 // Accumulator for work that is not cut into pieces of at most kFRMaxRun
-// entries (whole rows per lane, long rows strided over a warp): AccFR falls back
-// to AccFF there.
+// entries (whole rows per lane, long rows strided over a warp): AccFR and
+// AccFRF fall back to AccFF there.
 template <typename ACC> struct WholeRowAcc { using type = ACC; };
 template <> struct WholeRowAcc<AccFR> { using type = AccFF; };
+template <> struct WholeRowAcc<AccFRF> { using type = AccFF; };
+
+// Ends a block of at most kFRMaxRun entries (AccFRF: fold the run; others: nothing).
+template <typename ACC> __device__ __forceinline__ void end_run(ACC &) {}
+template <> __device__ __forceinline__ void end_run<AccFRF>(AccFRF &a) { a.fold(); }
 
 // Row r of m summed again with exact FP64 products of its (FP32-stored)
 // operands, in CRS order: the fallback for a poisoned float-float row sum (see
@@ -240,7 +270,8 @@ __device__ __forceinline__ double row_sum_exact(const MatRef m, int64_t r, const
 // again from the CRS arrays of m (row r, operand x); anything else as it is.
 template <typename VT, bool INDIRECT, typename XT, typename ACC>
 __device__ __forceinline__ double acc_value(const ACC &a, const MatRef &m, int64_t r, const XT *__restrict__ x) {
-    if constexpr (std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value) {
+    if constexpr (std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value ||
+                  std::is_same<ACC, AccFRF>::value) {
         if (a.poisoned()) return row_sum_exact<VT, INDIRECT>(m, r, x);
     }
     return a.get();

@@ -64,8 +64,8 @@ struct SellOps {
     int (*ctas_for)(int32_t n_slices);  // CTAs a launch over n_slices uses
 };
 // max_row: the longest row of the matrix; FP32 storage with the default
-// accumulator takes FP32 runs (AccFR) when no row exceeds 9 entries, else
-// float-float.
+// accumulator takes FP32 runs (AccFR) when no row exceeds 9 entries, else FP32
+// runs of one block folded into float-float (AccFRF).
 bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops, int32_t max_row = 0x7fffffff);
 // Block vectors on the sorted row slices, 4 right-hand sides:
 // Y[i*ldy + r] = alpha*sum_j a_ij X[j*ldx + r] + beta*Y[i*ldy + r], r = 0..3

@@ -1,7 +1,7 @@
 // Compiled configurations of the sorted row-slice kernel (plan family 5) and its
 // relayout kernel: FP64 values and vectors, and FP32 storage with FP32 runs
-// (every row at most 9 entries, so a lane's chain over a row is a run) or
-// float-float accumulation.
+// (every row at most 9 entries, so a lane's chain over a row is a run) or FP32
+// runs of one block (4 slot rows) each folded into float-float.
 #include "internal.h"
 #include "sell_kernel.cuh"
 
@@ -19,8 +19,8 @@ bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops, int32_t max_row) {
         return true;
     }
     if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF) {
-        ops->launch = &SellKernel<float, float, float, AccFF>::launch;
-        ops->ctas_for = &SellKernel<float, float, float, AccFF>::ctas_for;
+        ops->launch = &SellKernel<float, float, float, AccFRF>::launch;
+        ops->ctas_for = &SellKernel<float, float, float, AccFRF>::ctas_for;
         return true;
     }
     return false;

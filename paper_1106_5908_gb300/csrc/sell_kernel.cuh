@@ -83,7 +83,8 @@ __device__ __forceinline__ void sell_fma_tail(ACC (&acc)[kSellK], const VT (&v)[
 template <typename VT, typename XT, typename YT, typename ACC>
 __device__ __forceinline__ void sell_store(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y, int row,
                                            const ACC &a, double alpha, double beta, bool plain, double old) {
-    if constexpr ((std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value) &&
+    if constexpr ((std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value ||
+                   std::is_same<ACC, AccFRF>::value) &&
                   std::is_same<YT, float>::value) {
         if (plain && !a.poisoned()) {
             y[row] = a.h + a.l;
@@ -245,6 +246,8 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
             long_row<VT, XT, YT, ACC, false>(p.m, d, x, y, alpha, beta, plain, lane);
         } else {
             sell_fma_tail(acc, P.v, P.x, cnt_of(ca));
+#pragma unroll
+            for (int h = 0; h < K; ++h) end_run(acc[h]);
             if (last_of(ca)) {
 #pragma unroll
                 for (int h = 0; h < K; ++h) {

@@ -220,13 +220,18 @@ def test_fd_16cubed_fp32_storage():
     differences of f = g^T A(val) x computed by the library's own FP32-storage
     forward product (FP64 result): f is linear in each value and each x entry, so
     the quotient over the perturbation actually stored in FP32 is exact up to the
-    forward product's rounding.  Also against the oracle's reverse pass."""
+    forward product's rounding.  The forward runs with the FP64-FMA accumulator
+    (exact products summed in FP64, the definition of the FP32-storage form): the
+    quotient divides the forward's rounding by 2h = 0.02, and the default FP32-pipe
+    accumulator's bound (a few 1e-7 of sum |a x| per row) would dominate it.  Also
+    against the oracle's reverse pass."""
     A = W.stencil27(W.STENCIL27_FD_GRID, seed=W.SEED_STENCIL27_VAL)
     v32 = A.val.astype(np.float32)
     x32 = W.uniform(A.n_cols, W.SEED_STENCIL27_X).astype(np.float32)
     g32 = W.uniform(A.n_rows, W.SEED_STENCIL27_G).astype(np.float32)
     from paper_1106_5908_gb300 import Matrix
     M = Matrix.from_csr(A.row_ptr, A.col_idx, v32, A.n_cols)
+    M.set_accumulator("f64")
     gd = dev(g32).double()
     for alpha in (1.0, 1.25):
         M.set_values(dev(v32))

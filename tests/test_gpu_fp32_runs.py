@@ -187,3 +187,26 @@ def test_short_rows_out_of_fp32_range(plan):
             y = dev(yin)
             M.apply(dev(x), y, alpha, beta)
             check(host(y), ref, bound, out32, f"plan {plan} out {out} a={alpha} b={beta}")
+
+
+@pytest.mark.parametrize("sigma", [256, 4096])
+def test_row_slices_long_rows_within_gamma_4(sigma):
+    """27-point rows (up to 27 entries) on the row slices: FP32 runs of one block
+    (4 slot rows) folded into float-float, so every row within gamma_4 of the
+    oracle for any row length; and the reverse pass's row-slice copy of A^T."""
+    A = W.stencil27(14, seed=2)
+    rng = np.random.default_rng(sigma + 1)
+    v = wide(rng, A.nnz, -20.0, 20.0)
+    x = wide(rng, A.n_cols, -20.0, 20.0)
+    A32 = W.CRS(A.row_ptr, A.col_idx, v, A.n_cols)
+    M = make_plan(A32, (5, sigma))
+    ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v.astype(np.float64), x.astype(np.float64), with_bound=True)
+    y = host(M.apply(dev(x), out_dtype=torch.float64))
+    assert np.all(np.abs(y - ref) <= (gamma(4) + 2.0 ** -50) * bound)
+    g = wide(rng, A.n_rows, -20.0, 20.0)
+    gx_ref, _, gb = oracle.backward(A.row_ptr, A.col_idx, v.astype(np.float64), A.n_cols, g.astype(np.float64),
+                                    x.astype(np.float64), 1.0, with_bound=True)
+    for rep in range(2):
+        gx, _ = M.backward(dev(g), dev(x))
+        err = np.abs(host(gx).astype(np.float64) - gx_ref)
+        assert np.all(err <= (gamma(9) + 2.0 ** -50) * gb + U * (np.abs(gx_ref) + gamma(9) * gb) * 1.0001), rep
