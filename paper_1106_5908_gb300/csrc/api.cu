@@ -840,27 +840,38 @@ spmv_status prepare_run(spmv_matrix *h, int xk, int yk, int R, int E, bool trans
     return SPMV_OK;
 }
 
+// The row-slice launch of h for these operands (plan family 5, no row map):
+// its compiled configuration and parameters, with the slice copy built on first
+// use; false when h does not run on the row slices here.
+bool sell_launch_of(spmv_matrix *h, double alpha, const void *x, int xk, double beta, void *y, int yk,
+                    cudaStream_t s, SellOps *ops, SellParams *lp) {
+    if (h->family != 5 || h->d_rmap) return false;
+    const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
+    SellTable *lt = nullptr;
+    if (!sell_ops(h->vk, xk, yk, acc, ops, h->max_row) || (lt = get_sell(h, h->sigma, s)) == nullptr) return false;
+    *lp = SellParams{};
+    lp->slices = lt->d;
+    lp->srows = lt->srows;
+    lp->cstart = lt->cstart;
+    lp->n_ctas = lt->n_ctas;
+    lp->vals = lt->vals;
+    lp->cols = lt->cols;
+    lp->m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
+    lp->n_slices = lt->n;
+    lp->alpha = alpha;
+    lp->beta = beta;
+    return true;
+}
+
 spmv_status apply_impl(spmv_matrix *h, double alpha, const void *x, int xk, double beta, void *y,
                        int yk, cudaStream_t s) {
     if (h->n_rows == 0) return SPMV_OK;
     const int acc = (h->vk == kF32) ? h->acc32 : kAccF64;
-    if (h->family == 5 && !h->d_rmap) {
+    {
         SellOps lops;
-        SellTable *lt = nullptr;
-        if (sell_ops(h->vk, xk, yk, acc, &lops, h->max_row) && (lt = get_sell(h, h->sigma, s)) != nullptr) {
-            SellParams lp{};
-            lp.slices = lt->d;
-            lp.srows = lt->srows;
-            lp.cstart = lt->cstart;
-            lp.n_ctas = lt->n_ctas;
-            lp.vals = lt->vals;
-            lp.cols = lt->cols;
-            lp.m = MatRef{h->d_rp, h->d_col, h->d_val, nullptr, x, y, nullptr};
-            lp.n_slices = lt->n;
-            lp.alpha = alpha;
-            lp.beta = beta;
+        SellParams lp;
+        if (sell_launch_of(h, alpha, x, xk, beta, y, yk, s, &lops, &lp))
             return lops.launch(lp, s) == cudaSuccess ? SPMV_OK : SPMV_ERR_CUDA;
-        }
     }
     if (h->family == 6 && !h->d_rmap) {
         SlotOps tops;
@@ -2309,10 +2320,21 @@ spmv_status spmv_ir_cg(spmv_handle h, const double *b, double *x, double outer_t
         double rho = rho0;
         int32_t it = 0;
         auto inner_iter = [&](cudaStream_t cs) -> spmv_status {
-            spmv_status s2 = apply_impl(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, cs);
-            if (s2 != SPMV_OK) return s2;
-            if (cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, cs) != cudaSuccess ||
-                cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, cs) != cudaSuccess ||
+            // q = A p with p.q (and the step alpha) reduced by the product itself
+            // on the row slices; elsewhere the product, then the dot
+            SellOps lo;
+            SellParams lp;
+            if (sell_launch_of(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, cs, &lo, &lp) && lo.launch_dot &&
+                lp.n_slices > 0 && lp.n_ctas <= cg_partials_cap()) {
+                if (lo.launch_dot(lp, cg_red_out(w.partials, w.sc, kOpAlpha, 0), cs) != cudaSuccess)
+                    return SPMV_ERR_CUDA;
+            } else {
+                spmv_status s2 = apply_impl(A32, 1.0, w.p32, kF32, 0.0, w.q32, kF32, cs);
+                if (s2 != SPMV_OK) return s2;
+                if (cg_dot(w.p32, kF32, w.q32, kF32, n, w.partials, w.sc, kOpAlpha, 0, cs) != cudaSuccess)
+                    return SPMV_ERR_CUDA;
+            }
+            if (cg_update32(w.d32, w.r32, w.p32, w.q32, n, w.partials, w.sc, cs) != cudaSuccess ||
                 cg_direction(w.p32, w.r32, kF32, w.sc, n, cs) != cudaSuccess)
                 return SPMV_ERR_CUDA;
             return SPMV_OK;

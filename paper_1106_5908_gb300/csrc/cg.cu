@@ -10,69 +10,11 @@
 #include "internal.h"
 #include "common.cuh"
 #include "cg.h"
+#include "reduce.cuh"
 
 namespace spmv {
 
 constexpr int kDotThreads = 256;
-
-__device__ __forceinline__ double block_sum(double v, double *s_red) {
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) s_red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (w == 0) {
-        t = (lane < (int)(blockDim.x >> 5)) ? s_red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    }
-    __syncthreads();
-    return t;  // valid in thread 0
-}
-
-// Where a reduction ends: partials[gridDim.x], the ticket counting finished
-// blocks (zero between launches) and the scalar step op applied to the sum.
-struct RedOut {
-    double *partials;
-    unsigned int *ticket;
-    double *sc;
-    int op;
-    int dst;
-};
-
-__device__ __forceinline__ void apply_op(double t, double *sc, int op, int dst) {
-    if (op == kOpStore) {
-        sc[dst] = t;
-    } else if (op == kOpAlpha) {  // t = p.q; a zero direction (converged) takes no step
-        sc[kScPQ] = t;
-        sc[kScAlpha] = (t != 0.0) ? sc[kScRho] / t : 0.0;
-    } else if (op == kOpBeta) {   // t = r_new.r_new
-        sc[kScBeta] = (sc[kScRho] != 0.0) ? t / sc[kScRho] : 0.0;
-        sc[kScRho] = t;
-    }
-}
-
-// t: the block's partial (valid in thread 0).  The last block sums all partials
-// in block order, applies the step and re-arms the ticket.
-__device__ __forceinline__ void finish(double t, const RedOut &o, double *s_red) {
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        o.partials[blockIdx.x] = t;
-        __threadfence();
-        s_last = (atomicAdd(o.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < static_cast<int>(gridDim.x); i += blockDim.x) acc += __ldcg(o.partials + i);
-    const double tot = block_sum(acc, s_red);
-    if (threadIdx.x == 0) {
-        apply_op(tot, o.sc, o.op, o.dst);
-        *o.ticket = 0u;
-    }
-}
 
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(kDotThreads) k_dot(const TA *__restrict__ a,
@@ -312,13 +254,15 @@ static int red_grid(int64_t n) {
                                                                    int64_t(kRedBlocksPerSM) * sm_count())));
 }
 
-// partials (one per reduction block) followed by the ticket word
-int cg_partials_len() { return kRedBlocksPerSM * sm_count() + 2; }
+// partials (one per reduction block, room for 16 blocks per SM: the fused
+// product's persistent launch) followed by the ticket word
+int cg_partials_cap() { return 16 * sm_count(); }
+int cg_partials_len() { return cg_partials_cap() + 2; }
 
-static RedOut red_out(double *partials, double *sc, int op, int dst) {
-    return RedOut{partials, reinterpret_cast<unsigned int *>(partials + kRedBlocksPerSM * sm_count()), sc, op,
-                  dst};
+RedOut cg_red_out(double *partials, double *sc, int op, int dst) {
+    return RedOut{partials, reinterpret_cast<unsigned int *>(partials + cg_partials_cap()), sc, op, dst};
 }
+static RedOut red_out(double *partials, double *sc, int op, int dst) { return cg_red_out(partials, sc, op, dst); }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

@@ -10,8 +10,23 @@ enum : int { kScRho = 0, kScPQ = 1, kScAlpha = 2, kScBeta = 3, kScNorm = 4, kScC
 // Scalar steps applied after a reduction.
 enum : int { kOpStore = 0, kOpAlpha = 1, kOpBeta = 2 };
 
+// Where a reduction ends: partials (one per block), the ticket counting
+// finished blocks (zero between launches) and the scalar step op applied to
+// the sum, written to sc[dst] (kOpStore) or to the CG scalars.
+struct RedOut {
+    double *partials;
+    unsigned int *ticket;
+    double *sc;
+    int op;
+    int dst;
+};
+
 // doubles of the reduction work array (partials and the ticket word; zero it once)
 int cg_partials_len();
+// The reduction target in that work array for a launch of at most
+// cg_partials_cap() blocks.
+RedOut cg_red_out(double *partials, double *sc, int op, int dst);
+int cg_partials_cap();
 // sc[dst] = a.b (op kOpStore) or alpha = sc[rho]/(a.b) (op kOpAlpha).  FP64 accumulation.
 cudaError_t cg_dot(const void *a, int ak, const void *b, int bk, int64_t n, double *partials,
                    double *sc, int op, int dst, cudaStream_t s);

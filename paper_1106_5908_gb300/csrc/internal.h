@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "types.h"
+#include "cg.h"
 
 namespace spmv {
 
@@ -62,6 +63,9 @@ struct SellParams;
 struct SellOps {
     cudaError_t (*launch)(const SellParams &, cudaStream_t);
     int (*ctas_for)(int32_t n_slices);  // CTAs a launch over n_slices uses
+    // y = A x plus the dot x.y reduced into a CG reduction target (FP32
+    // storage only; nullptr elsewhere)
+    cudaError_t (*launch_dot)(const SellParams &, const RedOut &, cudaStream_t);
 };
 // max_row: the longest row of the matrix; FP32 storage with the default
 // accumulator takes FP32 runs (AccFR) when no row exceeds 9 entries, else FP32

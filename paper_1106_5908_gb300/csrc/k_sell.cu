@@ -11,16 +11,19 @@ bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops, int32_t max_row) {
     if (vk == kF64 && xk == kF64 && yk == kF64 && acc == kAccF64) {
         ops->launch = &SellKernel<double, double, double, AccF64>::launch;
         ops->ctas_for = &SellKernel<double, double, double, AccF64>::ctas_for;
+        ops->launch_dot = nullptr;
         return true;
     }
     if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF && max_row <= kFRMaxRun) {
         ops->launch = &SellKernel<float, float, float, AccFR>::launch;
         ops->ctas_for = &SellKernel<float, float, float, AccFR>::ctas_for;
+        ops->launch_dot = &SellKernel<float, float, float, AccFR>::launch_dot;
         return true;
     }
     if (vk == kF32 && xk == kF32 && yk == kF32 && acc == kAccFF) {
         ops->launch = &SellKernel<float, float, float, AccFRF>::launch;
         ops->ctas_for = &SellKernel<float, float, float, AccFRF>::ctas_for;
+        ops->launch_dot = &SellKernel<float, float, float, AccFRF>::launch_dot;
         return true;
     }
     return false;

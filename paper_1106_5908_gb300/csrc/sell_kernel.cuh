@@ -29,6 +29,7 @@
 // slot.
 #pragma once
 #include "slot_kernel.cuh"
+#include "reduce.cuh"
 
 namespace spmv {
 
@@ -81,14 +82,15 @@ __device__ __forceinline__ void sell_fma_tail(ACC (&acc)[kSellK], const VT (&v)[
 // (read only when beta is nonzero).  A poisoned float-float sum is summed again
 // in FP64 from the CRS arrays of m.
 template <typename VT, typename XT, typename YT, typename ACC>
-__device__ __forceinline__ void sell_store(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y, int row,
-                                           const ACC &a, double alpha, double beta, bool plain, double old) {
+__device__ __forceinline__ YT sell_store(const MatRef &m, const XT *__restrict__ x, YT *__restrict__ y, int row,
+                                         const ACC &a, double alpha, double beta, bool plain, double old) {
     if constexpr ((std::is_same<ACC, AccFF>::value || std::is_same<ACC, AccFR>::value ||
                    std::is_same<ACC, AccFRF>::value) &&
                   std::is_same<YT, float>::value) {
         if (plain && !a.poisoned()) {
-            y[row] = a.h + a.l;
-            return;
+            const float out = a.h + a.l;
+            y[row] = out;
+            return out;
         }
     }
     const double v = acc_value<VT, false>(a, m, row, x);
@@ -96,7 +98,9 @@ __device__ __forceinline__ void sell_store(const MatRef &m, const XT *__restrict
     if (plain) out = v;
     else if (beta == 0.0) out = alpha * v;
     else out = fma(alpha, v, beta * old);
-    y[row] = narrow<YT>(out);
+    const YT yo = narrow<YT>(out);
+    y[row] = yo;
+    return yo;
 }
 
 // Gather of x through L1, issued where it stands in the source (the compiler may
@@ -112,8 +116,11 @@ __device__ __forceinline__ float ld_gather(const float *p) {
     return v;
 }
 
-template <typename VT, typename XT, typename YT, typename ACC>
-__global__ void __launch_bounds__(256) k_sell(const SellParams p) {
+// The walk of one warp over its CTA's slices.  DOT: also dsum += x[r] * y[r]
+// (exact products of the stored values, FP64 sums) for every row r the warp
+// stores (the p.q of a CG step, with x = p and y = q).
+template <typename VT, typename XT, typename YT, typename ACC, bool DOT>
+__device__ __forceinline__ void sell_walk(const SellParams &p, double &dsum) {
     constexpr int U = kSellU, K = kSellK, C = kSellC;
     const int lane = threadIdx.x & 31;
     if (static_cast<int>(blockIdx.x) >= p.n_ctas) return;
@@ -244,6 +251,9 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
             const int row = ca.off;
             const ChunkDesc d{__ldg(p.m.rp + row), __ldg(p.m.rp + row + 1), row, (row + 1) | kChunkLong};
             long_row<VT, XT, YT, ACC, false>(p.m, d, x, y, alpha, beta, plain, lane);
+            if constexpr (DOT) {
+                if (lane == 0) dsum = fma(widen(x[row]), widen(y[row]), dsum);  // lane 0 stored it
+            }
         } else {
             sell_fma_tail(acc, P.v, P.x, cnt_of(ca));
 #pragma unroll
@@ -251,7 +261,10 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
             if (last_of(ca)) {
 #pragma unroll
                 for (int h = 0; h < K; ++h) {
-                    if (P.r[h] >= 0) sell_store<VT>(p.m, x, y, P.r[h], acc[h], alpha, beta, plain, P.y[h]);
+                    if (P.r[h] >= 0) {
+                        const YT q = sell_store<VT>(p.m, x, y, P.r[h], acc[h], alpha, beta, plain, P.y[h]);
+                        if constexpr (DOT) dsum = fma(widen(x[P.r[h]]), widen(q), dsum);
+                    }
                     acc[h].zero();
                 }
             }
@@ -265,6 +278,16 @@ __global__ void __launch_bounds__(256) k_sell(const SellParams p) {
         step(S0, S1);
         if (ca.s >= n) break;
         step(S1, S0);
+    }
+}
+
+template <typename VT, typename XT, typename YT, typename ACC, bool DOT = false>
+__global__ void __launch_bounds__(256) k_sell(const SellParams p, const RedOut o) {
+    double dsum = 0.0;
+    sell_walk<VT, XT, YT, ACC, DOT>(p, dsum);
+    if constexpr (DOT) {
+        __shared__ double s_red[32];
+        finish(block_sum(dsum, s_red), o, s_red);
     }
 }
 
@@ -515,7 +538,8 @@ struct SellKernel {
         if (cached >= 0 && cached_dev == dev) return cached;
         int per_sm = 0, sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<VT, XT, YT, ACC>, 256, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<VT, XT, YT, ACC, false>, 256, 0) !=
+            cudaSuccess)
             return 0;
         cached = per_sm * sms;
         cached_dev = dev;
@@ -531,7 +555,14 @@ struct SellKernel {
     }
     static cudaError_t launch(const SellParams &p, cudaStream_t s) {
         if (p.n_slices <= 0 || p.n_ctas <= 0) return cudaSuccess;
-        k_sell<VT, XT, YT, ACC><<<p.n_ctas, 256, 0, s>>>(p);
+        k_sell<VT, XT, YT, ACC, false><<<p.n_ctas, 256, 0, s>>>(p, RedOut{});
+        return cudaGetLastError();
+    }
+    // y = A x with the dot x.y reduced into o (the CG step's p.q); needs at least
+    // one slice and at most cg_partials_cap() CTAs
+    static cudaError_t launch_dot(const SellParams &p, const RedOut &o, cudaStream_t s) {
+        if (p.n_slices <= 0 || p.n_ctas <= 0 || p.n_ctas > cg_partials_cap()) return cudaErrorInvalidValue;
+        k_sell<VT, XT, YT, ACC, true><<<p.n_ctas, 256, 0, s>>>(p, o);
         return cudaGetLastError();
     }
 };
