@@ -210,3 +210,26 @@ def test_row_slices_long_rows_within_gamma_4(sigma):
         gx, _ = M.backward(dev(g), dev(x))
         err = np.abs(host(gx).astype(np.float64) - gx_ref)
         assert np.all(err <= (gamma(9) + 2.0 ** -50) * gb + U * (np.abs(gx_ref) + gamma(9) * gb) * 1.0001), rep
+
+
+def test_ir_cg_on_both_inner_paths():
+    """IR-CG takes q = A p with p.q reduced by the row-slice product itself when its
+    FP32 copy runs on the row slices (7-point matrix), and the product followed by
+    a separate dot otherwise (a scattered, diagonally dominant symmetric matrix on
+    the slot-major kernel): both converge to ||b - Ax|| <= 1e-12 ||b||, checked
+    by the oracle."""
+    from paper_1106_5908_gb300 import Matrix, ir_cg
+    H = W.hamiltonian_like(60000, seed=21)
+    rows = np.repeat(np.arange(H.n_rows), np.diff(H.row_ptr.astype(np.int64)))
+    off = rows != H.col_idx
+    v = H.val.copy()
+    rowabs = np.bincount(rows[off], weights=np.abs(v[off]), minlength=H.n_rows)
+    v[~off] = rowabs[rows[~off]] + 1.0  # diagonally dominant: SPD
+    S = W.CRS(H.row_ptr, H.col_idx, v, H.n_cols)
+    for A in (W.laplace3d(30), S):
+        M = Matrix.from_csr(A.row_ptr, A.col_idx, A.val, A.n_cols)
+        b = W.uniform(A.n_rows, 31)
+        x, st = ir_cg(M, dev(b), outer_tol=1e-12, max_outer=50)
+        assert st["converged"], st
+        r = oracle.residual(A.row_ptr, A.col_idx, A.val, b, host(x))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-12, st
