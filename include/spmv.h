@@ -135,11 +135,11 @@ spmv_status spmv_row_histogram(spmv_handle h, int32_t nbins, int64_t *counts);
  * family 3: three-stage warp-chunk kernel (gathers one chunk ahead), E = 7, 11, 15;
  * family 4: slot-major warp-chunk kernel (values and column indices copied once
  *           into chunk-major, lane-interleaved order and loaded coalesced into
- *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32: 7, 9, 15);
+ *           registers; no shared-memory staging), E = 7, 9, 11, 15 (FP32 as well);
  *           the copy is built on first use and its values follow spmv_set_values;
- *           with FP32 storage and E = 7 or 9 the default accumulator sums each
- *           lane's piece of a row (at most E entries) with FP32 FMAs and joins
- *           the pieces in float-float (see spmv_set_accumulator);
+ *           with FP32 storage and E = 7, 9 or 11 the default accumulator sums
+ *           each lane's piece of a row (at most E entries) with FP32 FMAs and
+ *           joins the pieces in float-float (see spmv_set_accumulator);
  * family 5: sorted row-slice kernel (SELL-C-sigma with C = 64: in each window
  *           of param rows, a power of two from 32 to 2^20, default 4096, the
  *           rows ordered by length and stored 64 rows at a time, two rows per
@@ -160,11 +160,12 @@ spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param);
 
 /* Accumulator of an FP32-storage handle: 0 = one FP64 FMA per entry (operands
  * widened exactly), 1 = FP32-pipe accumulation (default).  Setting 1 is, in the
- * slot-major kernel with E = 7 or 9 (family 4 and the batched launch), FP32
- * FMA runs over each lane's piece of a row (at most 9 products: error at most
- * gamma_9 = 9u/(1-9u) ~ 5.4e-7 of sum |a_ij x_j|, u = 2^-24) joined across lanes
- * by two-sum, and in the row-slice kernel (family 5) FP32 FMA runs over a whole
- * row of at most 9 entries or over blocks of 4 entries folded into float-float
+ * slot-major kernel with E = 7, 9 or 11 (family 4 and the batched launch), FP32
+ * FMA runs over each lane's piece of a row (at most E products: error at most
+ * gamma_E = E u/(1 - E u) of sum |a_ij x_j|, u = 2^-24: 5.4e-7 for E = 9, 6.6e-7
+ * for E = 11) joined across lanes by two-sum, and in the row-slice kernel
+ * (family 5) FP32 FMA runs over a whole row of at most 11 entries or over blocks
+ * of 4 entries folded into float-float
  * (gamma_4 ~ 2.4e-7); a row whose FP32 sum is not finite or below 2^-100 in
  * magnitude is summed again with FP64 FMAs.  Everywhere else it is exact-product
  * float-float accumulation (relative accuracy about 2^-44 of sum |a_ij x_j|),

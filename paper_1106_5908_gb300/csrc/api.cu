@@ -1309,7 +1309,6 @@ spmv_status spmv_set_plan(spmv_handle h, int32_t family, int32_t param) {
     }
     if (family == 4) {
         if (param != 0 && param != 7 && param != 9 && param != 11 && param != 15) return SPMV_ERR_INVALID_ARG;
-        if (h->vk == kF32 && param == 11) return SPMV_ERR_INVALID_ARG;
         h->family = 4;
         h->E = param ? param : (h->vk == kF32 ? 15 : 9);
         return SPMV_OK;

@@ -183,9 +183,9 @@ struct AccFF {
 
 // FP32 runs with float-float carries, for kernels whose lanes own at most
 // kFRMaxRun consecutive entries of a row (the slot-major chunk kernel with
-// E <= 9): the products of one lane's piece of a row are summed by plain FP32
-// FMAs (recursive summation, error at most gamma_k sum |a_ij x_j| with k <= 9
-// terms, gamma_k = k u / (1 - k u), u = 2^-24: 5.4e-7, inside the 1e-6 FP32-storage
+// E <= 11): the products of one lane's piece of a row are summed by plain FP32
+// FMAs (recursive summation, error at most gamma_k sum |a_ij x_j| with k <= 11
+// terms, gamma_k = k u / (1 - k u), u = 2^-24: 6.6e-7, inside the 1e-6 FP32-storage
 // tolerance), and the pieces of a row cut by lane boundaries are combined by
 // two-sum (float-float), whose error is of order u^2.  The bound assumes no
 // partial sum underflows or overflows; a row whose final sum is not finite or
@@ -193,7 +193,7 @@ struct AccFF {
 // small, or from exact cancellation) is marked poisoned and summed again with
 // FP64 products, as for AccFF.  Each entry costs one FP32 FMA instead of
 // AccFF's ten-odd FP32 operations.
-constexpr int kFRMaxRun = 9;
+constexpr int kFRMaxRun = 11;
 struct AccFR {
     float h, l;
     __device__ __forceinline__ void zero() { h = 0.f; l = 0.f; }

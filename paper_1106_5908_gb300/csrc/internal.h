@@ -68,7 +68,7 @@ struct SellOps {
     cudaError_t (*launch_dot)(const SellParams &, const RedOut &, cudaStream_t);
 };
 // max_row: the longest row of the matrix; FP32 storage with the default
-// accumulator takes FP32 runs (AccFR) when no row exceeds 9 entries, else FP32
+// accumulator takes FP32 runs (AccFR) when no row exceeds 11 entries, else FP32
 // runs of one block folded into float-float (AccFRF).
 bool sell_ops(int vk, int xk, int yk, int acc, SellOps *ops, int32_t max_row = 0x7fffffff);
 // Block vectors on the sorted row slices, 4 right-hand sides:

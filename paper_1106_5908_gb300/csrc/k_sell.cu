@@ -1,6 +1,6 @@
 // Compiled configurations of the sorted row-slice kernel (plan family 5) and its
 // relayout kernel: FP64 values and vectors, and FP32 storage with FP32 runs
-// (every row at most 9 entries, so a lane's chain over a row is a run) or FP32
+// (every row at most 11 entries, so a lane's chain over a row is a run) or FP32
 // runs of one block (4 slot rows) each folded into float-float.
 #include "internal.h"
 #include "sell_kernel.cuh"

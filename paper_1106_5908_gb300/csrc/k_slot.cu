@@ -1,6 +1,6 @@
 // Compiled configurations of the slot-major chunk kernel (plan family 4) and its
 // relayout kernel: FP64 values and vectors, and FP32 storage with FP32 runs and
-// float-float carries (E = 7, 9: at most 9 entries of a row per lane) or
+// float-float carries (E = 7, 9, 11: at most 11 entries of a row per lane) or
 // float-float accumulation (E = 15).
 #include "internal.h"
 #include "slot_kernel.cuh"
@@ -48,6 +48,7 @@ bool slot_ops(int vk, int xk, int yk, int acc, int E, bool pre, SlotOps *ops) {
     SPMV_S(kF64, kF64, kF64, kAccF64, 15, double, double, double, AccF64)
     SPMV_S(kF32, kF32, kF32, kAccFF, 7, float, float, float, AccFR)
     SPMV_S(kF32, kF32, kF32, kAccFF, 9, float, float, float, AccFR)
+    SPMV_S(kF32, kF32, kF32, kAccFF, 11, float, float, float, AccFR)
     SPMV_S(kF32, kF32, kF32, kAccFF, 15, float, float, float, AccFF)
 #undef SPMV_S
     return false;

@@ -218,7 +218,7 @@ __device__ __forceinline__ void slot_loop(const SlotParams &p, ACC *srow, int c,
 // 80 it spills: 256 matrices 0.85 against 0.655 ms).
 template <int E, typename VT, bool BATCHED>
 constexpr int slot_min_ctas() {
-    return sizeof(VT) == 8 ? (E <= 11 ? 2 : 1) : ((E <= 9 && !BATCHED) ? 3 : 1);
+    return sizeof(VT) == 8 ? (E <= 11 ? 2 : 1) : ((E <= 9 && !BATCHED) ? 3 : ((E <= 11 && !BATCHED) ? 2 : 1));
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool PRE = false, bool BATCHED = false>

@@ -41,7 +41,7 @@ def wide(rng, n, lo, hi):
     return (mag * np.where(rng.random(n) < 0.5, -1.0, 1.0)).astype(np.float32)
 
 
-@pytest.mark.parametrize("E", [7, 9])
+@pytest.mark.parametrize("E", [7, 9, 11])
 @pytest.mark.parametrize("spread", [0.0, 24.0])
 def test_error_within_gamma_E(E, spread):
     """Values and x with magnitudes spread over 2^+-spread (cancellation inside
@@ -66,7 +66,7 @@ def test_error_within_gamma_E(E, spread):
     assert bad.size == 0, bad[:5]
 
 
-@pytest.mark.parametrize("E", [7, 9])
+@pytest.mark.parametrize("E", [7, 9, 11])
 def test_rows_summing_to_zero_are_exact(E):
     """A 2D Laplacian times a constant vector: interior rows sum to exactly 0 (a
     zero FP32 sum is re-summed in FP64), boundary rows to small integers: the
@@ -85,7 +85,7 @@ def test_rows_summing_to_zero_are_exact(E):
     assert np.array_equal(host(yd), ref2)
 
 
-@pytest.mark.parametrize("E", [7, 9])
+@pytest.mark.parametrize("E", [7, 9, 11])
 def test_integer_values_bit_exact(E):
     """Integer values and x with every partial sum below 2^24: exact in FP32 runs
     and in the float-float joins, so bit-exact against the oracle."""
@@ -115,7 +115,7 @@ def test_long_rows_use_float_float():
     v = wide(rng, int(rp[-1]), -12.0, 12.0)
     A = W.CRS(rp.astype(np.int32), col, v, n)
     x = wide(rng, n, -12.0, 12.0)
-    for E in (7, 9):
+    for E in (7, 9, 11):
         M = make32(A, E)
         ref, bound = oracle.spmv(A.row_ptr, A.col_idx, v.astype(np.float64), x.astype(np.float64), with_bound=True)
         y = host(M.apply(dev(x), out_dtype=torch.float64))
