@@ -257,24 +257,30 @@ __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&x
     // row-end test costs them 3-6 %), so the last store of a row is its full sum
     constexpr bool kRowEndStores = !std::is_same<ACC, AccFF>::value;
     static_assert(!std::is_same<ACC, AccFR>::value || E <= kFRMaxRun, "FP32 runs of at most kFRMaxRun entries");
+    // per-slot decisions as bit masks, formed once: capm = the slot before which
+    // the piece of a row begun in an earlier lane ends (the first row start
+    // after slot lo, unless slot lo starts one); startm = the slots at and
+    // after the first row start of the lane; storem = the slots whose running
+    // sum is stored
+    const uint32_t low = flush & (0u - flush);
+    const uint32_t capm = starts_first ? 0u : low;
+    const uint32_t startm = starts_first ? span : (low ? (span & ~(low - 1u)) : 0u);
+    const uint32_t storem = kRowEndStores ? (endm & startm) : startm;
+    const bool started = startm != 0u;  // a row starts in the lane's slots
     ACC acc;
     acc.zero();
     ACC pend;
     pend.zero();
-    bool started = starts_first;
-    bool has_pend = false;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const bool b = (flush >> e) & 1u;
-        const bool cap = b && !started;
-        if (cap) pend = acc;
-        has_pend = has_pend || cap;
+        if ((capm >> e) & 1u) pend = acc;
         if (b) acc.zero();
         row += b ? 1 : 0;
-        started = started || b;
         acc.fma(vals[e], xv[e]);
-        if (kRowEndStores ? (started && ((endm >> e) & 1u)) : started) srow[row - r0] = acc;
+        if ((storem >> e) & 1u) srow[row - r0] = acc;
     }
+    bool has_pend = capm != 0u;
     if (active && !started && ends) {
         pend = acc;
         has_pend = true;
