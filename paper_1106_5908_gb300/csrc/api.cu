@@ -221,11 +221,19 @@ void make_slot_chunks(const int32_t *rp, int32_t n_rows, int E, std::vector<Chun
         if (!empty) {
             const int64_t n_used = static_cast<int64_t>(rp[r1]) - k0;
             uint32_t pre = 0;
+            int through_run = 0;  // lanes just before this one that lie inside one row
             for (int lane = 0; lane < 32; ++lane) {
                 const uint32_t bits = lmask[mo + lane];
+                const bool active = static_cast<int64_t>(lane) * E < n_used;
                 const bool ends = static_cast<int64_t>(lane + 1) * E >= n_used ||
                                   (lane < 31 && (lmask[mo + lane + 1] & 1u));
-                lmask[mo + lane] = bits | (pre << kSlotPreShift) | (ends ? kSlotEnds : 0u);
+                const bool started = bits != 0u;
+                // a piece of a row begun in an earlier lane ends in this lane
+                const bool pending = active && !(bits & 1u) && (started || ends);
+                const uint32_t chain = pending ? static_cast<uint32_t>(1 + through_run) : 0u;
+                through_run = (active && !ends && !started) ? through_run + 1 : 0;
+                lmask[mo + lane] = bits | (pre << kSlotPreShift) | (ends ? kSlotEnds : 0u) |
+                                   (chain << kSlotChainShift);
                 pre += static_cast<uint32_t>(__builtin_popcount(bits));
             }
         }

@@ -23,6 +23,11 @@ namespace spmv {
 constexpr int kSlotPreShift = 16;
 constexpr uint32_t kSlotPreMask = 0x7fu;
 constexpr uint32_t kSlotEnds = 1u << 23;
+// bits 24-28: the lane's carry chain, how many earlier lanes' sums it adds (1
+// + the lanes just before it that lie inside one row, 0 when its first slot
+// starts a row or it holds no entries)
+constexpr int kSlotChainShift = 24;
+constexpr uint32_t kSlotChainMask = 0x1fu;
 
 struct SlotParams {
     const ChunkDesc *chunks;
@@ -181,11 +186,13 @@ __device__ __forceinline__ void slot_loop(const SlotParams &p, ACC *srow, int c,
             if constexpr (kSlotScan<E, VT, PRE>::value) {
                 const uint32_t next_bits = __shfl_down_sync(0xffffffffu, mbits, 1);
                 const bool ends = (lane * E + E >= dc.k1 - dc.k0) || (lane < 31 && (next_bits & 1u));
-                chunk_lane<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, ends, r0, srow, lane);
+                chunk_lane<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, ends, r0, srow, lane,
+                                           static_cast<int>((mc >> kSlotChainShift) & kSlotChainMask));
             } else {
                 chunk_lane_pre<E, VT, XT, ACC>(vc, xc, mbits, 0, hi, (mc & kSlotEnds) != 0u,
                                                static_cast<int>((mc >> kSlotPreShift) & kSlotPreMask), r0,
-                                               srow, lane);
+                                               srow, lane,
+                                               static_cast<int>((mc >> kSlotChainShift) & kSlotChainMask));
             }
             __syncwarp();
             if constexpr (PRE) {

@@ -240,7 +240,7 @@ __device__ __forceinline__ void rows_per_lane(const MatRef &m, int r0, int r1, c
 template <int E, typename VT, typename XT, typename ACC>
 __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
                                                int lo, int hi, bool ends, int pre, int r0, ACC *srow,
-                                               int lane) {
+                                               int lane, int chain = -1) {
     const bool active = lo < hi;
     const bool starts_first = active && ((mbits >> lo) & 1u);
     int row = r0 + pre + (starts_first ? 1 : 0) - 1;  // row of slot lo
@@ -288,18 +288,33 @@ __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&x
     const bool carry = active && !ends;
     const bool through = carry && !started;  // the lane's slots lie inside one row
     ACC tot = pend;
-    int dist = 1;
-    bool need = has_pend;
-    while (__any_sync(0xffffffffu, need)) {
-        const ACC c = shfl_up_acc(acc, dist);
-        const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
-        if (need) {
-            ACC t2 = c;
-            t2.add(tot);
-            tot = t2;
-            need = cthrough;
+    if (chain >= 0) {
+        // chain: how many earlier lanes' sums this lane adds (from the host: 1 +
+        // the through lanes just before it, 0 without a pending piece); the
+        // warp runs the longest chain, with no vote per step
+        const int longest = __reduce_max_sync(0xffffffffu, chain);
+        for (int dist = 1; dist <= longest; ++dist) {
+            const ACC c = shfl_up_acc(acc, dist);
+            if (dist <= chain) {
+                ACC t2 = c;
+                t2.add(tot);
+                tot = t2;
+            }
         }
-        ++dist;
+    } else {
+        int dist = 1;
+        bool need = has_pend;
+        while (__any_sync(0xffffffffu, need)) {
+            const ACC c = shfl_up_acc(acc, dist);
+            const bool cthrough = __shfl_up_sync(0xffffffffu, through, dist);
+            if (need) {
+                ACC t2 = c;
+                t2.add(tot);
+                tot = t2;
+                need = cthrough;
+            }
+            ++dist;
+        }
     }
     if (has_pend) srow[first_row - r0] = tot;
 }
@@ -307,7 +322,8 @@ __device__ __forceinline__ void chunk_lane_pre(const VT (&vals)[E], const XT (&x
 // As chunk_lane_pre, with `pre` from a shuffle scan of the lanes' row-start counts.
 template <int E, typename VT, typename XT, typename ACC>
 __device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E], uint32_t mbits,
-                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane) {
+                                           int lo, int hi, bool ends, int r0, ACC *srow, int lane,
+                                           int chain = -1) {
     const int cnt = __popc(mbits);
     int pre = cnt;
 #pragma unroll
@@ -316,7 +332,7 @@ __device__ __forceinline__ void chunk_lane(const VT (&vals)[E], const XT (&xv)[E
         if (lane >= o) pre += t;
     }
     pre -= cnt;
-    chunk_lane_pre<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, pre, r0, srow, lane);
+    chunk_lane_pre<E, VT, XT, ACC>(vals, xv, mbits, lo, hi, ends, pre, r0, srow, lane, chain);
 }
 
 template <int E, typename VT, typename XT, typename YT, typename ACC, bool INDIRECT, bool BATCHED>
